@@ -1,0 +1,183 @@
+/*
+ * mbe.h -- C ABI of the GB300 MBE-FCI hot path.
+ *
+ * Many-body expanded full configuration interaction with a (multi-
+ * determinantal) CAS expansion reference, Eriksen & Gauss, "Many-Body
+ * Expanded Full Configuration Interaction. II. Strongly Correlated Regime"
+ * (arXiv:1905.02786), Sec. 2:
+ *   Eq. 1  E = sum over orders of the increments,
+ *   Eq. 2  increment of a tuple = its CASCI energy minus those of all proper
+ *          subtuples (S_m = unique subtuples of length m),
+ *   Eq. 3  the same with a reference space Pi: every CASCI correlates Pi plus
+ *          the tuple; the order-0 term is the CASCI energy of Pi,
+ *   Fig. 2 occupied orbitals outside Pi+tuple are inactive (doubly
+ *          occupied), virtuals outside it are deleted.
+ *
+ * Every CASCI is solved on the GPU by a Davidson iteration on a
+ * string-driven sigma vector; increments are assembled through a device
+ * hash of tuples and screened; the energy gradient is assembled from the
+ * tuples' RDMs (Hellmann-Feynman).
+ *
+ * General conventions
+ *  - Return value: MBE_OK (0) or a negative MBE_E* code; the message of the
+ *    last failure of a context is returned by mbe_last_error().
+ *  - Ownership: every array argument is caller-owned HOST memory unless the
+ *    name ends in _dev (caller-owned DEVICE memory on the context's device).
+ *    Inputs are copied before the call returns; the library never keeps a
+ *    caller pointer.
+ *  - Threads: a context is not thread-safe; use one context per host thread.
+ *  - Orbitals are 0-based; orbitals 0 .. nelec/2-1 are the occupied ones of
+ *    the closed-shell (RHF-like) reference determinant.  norb <= 128.
+ *  - Integrals are real: h is norb x norb row-major (symmetric); the
+ *    two-electron integrals (pq|rs) (chemists' notation, 8-fold symmetric)
+ *    are passed packed 4-fold as a symmetric npair x npair row-major matrix
+ *    eri[P*npair + Q], npair = norb(norb+1)/2, P = p(p+1)/2 + q for p >= q.
+ *  - Energies are total electronic energies in Eh (the paper's correlation
+ *    energies differ by a constant, which affects only the order-0 term).
+ *  - State: the lowest singlet (S = 0, Ms = 0) of each CASCI.
+ */
+#ifndef MBE_H
+#define MBE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  MBE_OK = 0,
+  MBE_EINVAL = -1,    /* bad argument (size, index, NaN/Inf input, order)   */
+  MBE_ENOMEM = -2,    /* device allocation failed or memory cap exceeded    */
+  MBE_ECUDA = -3,     /* a CUDA runtime call failed                          */
+  MBE_ENOCONV = -4,   /* some CASCI did not converge (see status_out)       */
+  MBE_ELOOKUP = -5,   /* a subtuple increment was missing from the hash     */
+  MBE_ESTATE = -6     /* call out of sequence (e.g. no integrals loaded)    */
+};
+
+/* Precision of the sigma-vector contraction. */
+enum {
+  MBE_FP64 = 0,        /* every step in FP64                                 */
+  MBE_MIXED_BF16X3 = 1 /* sigma contraction as split-BF16x3 on tcgen05 tensor
+                          cores with FP32 accumulation; Rayleigh-Ritz,
+                          orthogonalisation, final Rayleigh quotient and sums
+                          in FP64                                            */
+};
+
+typedef struct mbe_options {
+  int precision;        /* MBE_FP64 or MBE_MIXED_BF16X3                      */
+  int max_batch;        /* max tuples solved together in one bin (>= 1); 1
+                           gives the one-tuple-at-a-time path               */
+  int max_subspace;     /* Davidson subspace size before restart (4..32)     */
+  int max_iter;         /* Davidson iteration cap per tuple                  */
+  double conv_tol_r;    /* residual-norm tolerance of the Davidson iteration */
+  double conv_tol_e;    /* energy-change tolerance                           */
+  double spin_shift;    /* lambda of H + lambda S^2 (lifts S >= 2 states)    */
+  int keep_ci;          /* keep converged CI vectors for the energy backward */
+  int deterministic;    /* 1: fixed-order reductions only (no float atomics) */
+  int64_t mem_cap_bytes;/* cap on device memory the context may allocate; 0 =
+                           no cap (exceeding it returns MBE_ENOMEM)          */
+} mbe_options;
+
+typedef struct mbe_ctx mbe_ctx;
+
+/* Counters accumulated by a context since creation or mbe_reset_stats. */
+typedef struct mbe_stats {
+  int64_t casci;          /* CASCI problems solved                            */
+  int64_t sigma_vectors;  /* sigma-vector applications inside Davidson        */
+  double sigma_flops;     /* algorithmic flops of the (kl|ij) contraction,
+                             2 * N_det * npair^2 per sigma vector             */
+  int64_t iters_total;    /* Davidson iterations summed over CASCIs           */
+  int64_t iters_max;      /* largest iteration count of one CASCI             */
+  int64_t noconv;         /* CASCIs that hit the iteration cap                */
+} mbe_stats;
+
+/* Fill *opt with the defaults (FP64, max_batch 256, subspace 16, 200
+ * iterations, tol_r 1e-8, tol_e 1e-12, spin_shift 0.5, keep_ci 0,
+ * deterministic 1, no memory cap). */
+void mbe_default_options(mbe_options* opt);
+
+/* Create a context on CUDA device `device`.  opt may be NULL (defaults).
+ * The context owns its device memory and a CUDA stream. */
+int mbe_create(mbe_ctx** out, int device, const mbe_options* opt);
+void mbe_destroy(mbe_ctx* ctx);
+const char* mbe_last_error(const mbe_ctx* ctx);
+
+/* Load the molecular integrals (input of every CASCI of Sec. 2).
+ *  norb   number of spatial orbitals (1..128)
+ *  nelec  number of (correlated) electrons, even (closed-shell reference)
+ *  h      norb*norb, eri npair*npair (see conventions); NaN/Inf -> EINVAL.
+ * Resets the reference space, the increment hash and kept CI vectors. */
+int mbe_load_integrals(mbe_ctx* ctx, int norb, int nelec, const double* h,
+                       const double* eri);
+
+/* Set the reference space Pi (Sec. 2, Eq. 3) and the expansion space.
+ *  ref_orbs[nref]  orbitals of Pi (distinct, any order)
+ *  exp_orbs[nexp]  expansion orbitals (distinct, disjoint from Pi)
+ * Solves the order-0 CASCI of Pi; its energy is written to *e_ref (may be
+ * NULL).  Resets the increment hash. */
+int mbe_set_reference(mbe_ctx* ctx, const int* ref_orbs, int nref,
+                      const int* exp_orbs, int nexp, double* e_ref);
+
+/* Solve the CASCI of every tuple (Sec. 2: active space = Pi + tuple).
+ *  order        tuple length n >= 1
+ *  tuples       ntup*order expansion orbitals, each row strictly ascending
+ *  e_out        ntup total CASCI energies eps_T (may be NULL)
+ *  status_out   ntup per-tuple status (0 converged, MBE_ENOCONV) (may be NULL)
+ * The tuples become the "current order" consumed by mbe_increments.
+ * Returns MBE_ENOCONV if any tuple did not converge (energies still
+ * written). */
+int mbe_solve_tuples(mbe_ctx* ctx, int order, const int32_t* tuples,
+                     int64_t ntup, double* e_out, int32_t* status_out);
+
+/* Increments of the current order (Eq. 3) by hash lookup of all proper
+ * non-empty subtuples (all lower orders must have been processed, in
+ * order), insertion of the new increments, screening and the order sum.
+ *  screen_thr  |increment| >= screen_thr marks a tuple "kept" (may spawn
+ *              children); 0 keeps all
+ *  inc_out     ntup increments (may be NULL)
+ *  keep_out    ntup flags (may be NULL)
+ *  e_order_out Kahan sum of the order's increments (may be NULL)
+ *  e_total_out eps_Pi + Kahan sum of all order sums so far (may be NULL)
+ * Returns MBE_ELOOKUP if a subtuple is missing. */
+int mbe_increments(mbe_ctx* ctx, int order, double screen_thr, double* inc_out,
+                   uint8_t* keep_out, double* e_order_out, double* e_total_out);
+
+/* Tuples of order `order` (>= 2) generated on the device from the last
+ * processed order by the screening rule: a tuple is formed iff every one of
+ * its (order-1)-subtuples exists and at least one of them is kept.  For
+ * order 1 every expansion orbital.  Lexicographic order.
+ *  tuples_out  capacity cap rows of `order` int32 (may be NULL to count)
+ *  ntup_out    number of tuples (always written)
+ * Returns MBE_EINVAL if cap is too small (ntup_out still written). */
+int mbe_next_tuples(mbe_ctx* ctx, int order, int32_t* tuples_out, int64_t cap,
+                    int64_t* ntup_out);
+
+/* Gradient of the MBE energy (eps_Pi + all increments processed so far)
+ * with respect to the integrals, by Hellmann-Feynman: each CASCI energy is
+ * stationary in its CI coefficients, so dE/dh_pq = sum_T c_T gamma^T_pq and
+ * dE/d(pq|rs) = 1/2 sum_T c_T Gamma^T_pqrs, with full-space spin-summed RDMs
+ * (inactive core included) and c_T = sum_{U in set, U >= T} (-1)^{|U|-|T|}.
+ * Needs keep_ci = 1 when the tuples were solved.
+ *  scale  multiplies the outputs (the incoming dL/dE)
+ *  dh     norb*norb (symmetric)
+ *  deri   npair*npair, gradient w.r.t. the symmetric packed eri matrix
+ *         (sum over the full-tensor images of (P,Q), symmetrised P<->Q). */
+int mbe_energy_backward(mbe_ctx* ctx, double scale, double* dh, double* deri);
+
+/* Copy the context's counters to *out (host). */
+int mbe_get_stats(const mbe_ctx* ctx, mbe_stats* out);
+/* Zero the context's counters. */
+int mbe_reset_stats(mbe_ctx* ctx);
+
+/* Sigma vector of one CASCI for testing: sigma = (H_active + spin_shift*S^2)
+ * c in the determinant basis of strings (Ia, Ib), in the context precision.
+ *  act[nact]  active orbitals; c, sigma  nstr*nstr (host)
+ * H_active excludes the inactive-core energy (returned in *e_core). */
+int mbe_sigma(mbe_ctx* ctx, const int* act, int nact, const double* c,
+              double* sigma, double* e_core);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MBE_H */

@@ -1,0 +1,240 @@
+"""Thin ctypes binding of libmbe (include/mbe.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts NumPy
+arrays to pointers, checks return codes and raises ``MBEError`` with the
+library's message.  The library must have been built
+(``paper_1905_02786_gb300.build.build()``); a missing library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libmbe.so")
+
+MBE_OK, MBE_EINVAL, MBE_ENOMEM, MBE_ECUDA, MBE_ENOCONV, MBE_ELOOKUP, MBE_ESTATE = \
+    0, -1, -2, -3, -4, -5, -6
+MBE_FP64, MBE_MIXED_BF16X3 = 0, 1
+ERROR_NAMES = {0: "MBE_OK", -1: "MBE_EINVAL", -2: "MBE_ENOMEM", -3: "MBE_ECUDA",
+               -4: "MBE_ENOCONV", -5: "MBE_ELOOKUP", -6: "MBE_ESTATE"}
+
+EXPORTED = ["mbe_default_options", "mbe_create", "mbe_destroy", "mbe_last_error",
+            "mbe_load_integrals", "mbe_set_reference", "mbe_solve_tuples",
+            "mbe_increments", "mbe_next_tuples", "mbe_energy_backward", "mbe_sigma",
+            "mbe_get_stats", "mbe_reset_stats"]
+
+
+class MBEError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class mbe_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("max_batch", ctypes.c_int),
+                ("max_subspace", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("conv_tol_r", ctypes.c_double), ("conv_tol_e", ctypes.c_double),
+                ("spin_shift", ctypes.c_double), ("keep_ci", ctypes.c_int),
+                ("deterministic", ctypes.c_int), ("mem_cap_bytes", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libmbe.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"libmbe.so not found at {path}: run paper_1905_02786_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    c_int, c_double, c_i64 = ctypes.c_int, ctypes.c_double, ctypes.c_int64
+    vp = ctypes.c_void_p
+    L.mbe_default_options.argtypes = [ctypes.POINTER(mbe_options)]
+    L.mbe_default_options.restype = None
+    L.mbe_create.argtypes = [ctypes.POINTER(vp), c_int, ctypes.POINTER(mbe_options)]
+    L.mbe_destroy.argtypes = [vp]
+    L.mbe_destroy.restype = None
+    L.mbe_last_error.argtypes = [vp]
+    L.mbe_last_error.restype = ctypes.c_char_p
+    L.mbe_load_integrals.argtypes = [vp, c_int, c_int, vp, vp]
+    L.mbe_set_reference.argtypes = [vp, vp, c_int, vp, c_int, vp]
+    L.mbe_solve_tuples.argtypes = [vp, c_int, vp, c_i64, vp, vp]
+    L.mbe_increments.argtypes = [vp, c_int, c_double, vp, vp, vp, vp]
+    L.mbe_next_tuples.argtypes = [vp, c_int, vp, c_i64, vp]
+    L.mbe_energy_backward.argtypes = [vp, c_double, vp, vp]
+    L.mbe_sigma.argtypes = [vp, vp, c_int, vp, vp, vp]
+    for name in EXPORTED:
+        if name not in ("mbe_default_options", "mbe_destroy", "mbe_last_error",
+                        "mbe_get_stats", "mbe_reset_stats"):
+            getattr(L, name).restype = c_int
+    _lib = L
+    return L
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(ctx, rc, allow=()):
+    if rc != MBE_OK and rc not in allow:
+        msg = load_library().mbe_last_error(ctx).decode() if ctx else "no context"
+        raise MBEError(rc, msg)
+    return rc
+
+
+def mbe_default_options() -> mbe_options:
+    o = mbe_options()
+    load_library().mbe_default_options(ctypes.byref(o))
+    return o
+
+
+def mbe_create(device: int = 0, options: mbe_options | None = None):
+    L = load_library()
+    h = ctypes.c_void_p()
+    rc = L.mbe_create(ctypes.byref(h), device, ctypes.byref(options) if options else None)
+    if rc != MBE_OK:
+        raise MBEError(rc, "mbe_create failed")
+    return h
+
+
+def mbe_destroy(ctx):
+    load_library().mbe_destroy(ctx)
+
+
+def mbe_last_error(ctx) -> str:
+    return load_library().mbe_last_error(ctx).decode()
+
+
+def mbe_load_integrals(ctx, h, eri, nelec: int):
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    eri = np.ascontiguousarray(eri, dtype=np.float64)
+    norb = h.shape[0]
+    return _check(ctx, load_library().mbe_load_integrals(ctx, norb, int(nelec), _p(h), _p(eri)))
+
+
+def mbe_set_reference(ctx, ref, exp) -> float:
+    ref = np.ascontiguousarray(ref, dtype=np.int32)
+    exp = np.ascontiguousarray(exp, dtype=np.int32)
+    e = np.zeros(1)
+    _check(ctx, load_library().mbe_set_reference(ctx, _p(ref), ref.size, _p(exp), exp.size, _p(e)))
+    return float(e[0])
+
+
+def mbe_solve_tuples(ctx, tuples, order: int | None = None, allow_noconv=False):
+    t = np.ascontiguousarray(tuples, dtype=np.int32)
+    if t.ndim == 1:
+        t = t.reshape(-1, order or 1)
+    ntup, order = t.shape[0], (order or t.shape[1])
+    eps = np.zeros(ntup)
+    st = np.zeros(ntup, dtype=np.int32)
+    _check(ctx, load_library().mbe_solve_tuples(ctx, order, _p(t), ntup, _p(eps), _p(st)),
+           allow=(MBE_ENOCONV,) if allow_noconv else ())
+    return eps, st
+
+
+def mbe_increments(ctx, order: int, screen_thr: float, ntup: int):
+    inc = np.zeros(max(ntup, 1))
+    keep = np.zeros(max(ntup, 1), dtype=np.uint8)
+    eo = np.zeros(1)
+    et = np.zeros(1)
+    _check(ctx, load_library().mbe_increments(ctx, order, float(screen_thr), _p(inc), _p(keep),
+                                              _p(eo), _p(et)))
+    return inc[:ntup], keep[:ntup].astype(bool), float(eo[0]), float(et[0])
+
+
+def mbe_next_tuples(ctx, order: int):
+    n = np.zeros(1, dtype=np.int64)
+    L = load_library()
+    _check(ctx, L.mbe_next_tuples(ctx, order, None, 0, _p(n)))
+    out = np.zeros((max(int(n[0]), 1), order), dtype=np.int32)
+    _check(ctx, L.mbe_next_tuples(ctx, order, _p(out), int(n[0]), _p(n)))
+    return out[: int(n[0])]
+
+
+def mbe_energy_backward(ctx, norb: int, scale: float = 1.0):
+    npair = norb * (norb + 1) // 2
+    dh = np.zeros((norb, norb))
+    dg = np.zeros((npair, npair))
+    _check(ctx, load_library().mbe_energy_backward(ctx, float(scale), _p(dh), _p(dg)))
+    return dh, dg
+
+
+def mbe_sigma(ctx, act, c):
+    act = np.ascontiguousarray(sorted(act), dtype=np.int32)
+    c = np.ascontiguousarray(c, dtype=np.float64).ravel()
+    sig = np.zeros_like(c)
+    ec = np.zeros(1)
+    _check(ctx, load_library().mbe_sigma(ctx, _p(act), act.size, _p(c), _p(sig), _p(ec)))
+    return sig, float(ec[0])
+
+
+class MBE:
+    """Convenience owner of one context; runs whole expansions through the
+    C ABI (host loop over orders: next tuples -> solve -> increments)."""
+
+    def __init__(self, device=0, **opts):
+        o = mbe_default_options()
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(o, k, v)
+        self.options = o
+        self.ctx = mbe_create(device, o)
+
+    def close(self):
+        if self.ctx:
+            mbe_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, h, eri, nelec):
+        mbe_load_integrals(self.ctx, h, eri, nelec)
+        self.norb = h.shape[0]
+
+    def run(self, ref, exp, max_order, thr=0.0, callback=None):
+        """Full expansion; returns dict(eps_ref, orders=[...], total)."""
+        e_ref = mbe_set_reference(self.ctx, ref, exp)
+        orders = []
+        total = e_ref
+        for k in range(1, max_order + 1):
+            tuples = mbe_next_tuples(self.ctx, k)
+            if len(tuples) == 0:
+                break
+            eps, st = mbe_solve_tuples(self.ctx, tuples, k)
+            inc, keep, e_order, total = mbe_increments(self.ctx, k, thr, len(tuples))
+            rec = dict(order=k, tuples=tuples, eps=eps, status=st, inc=inc, keep=keep,
+                       E_order=e_order)
+            orders.append(rec)
+            if callback:
+                callback(rec)
+        return dict(eps_ref=e_ref, orders=orders, total=total)
+
+
+class mbe_stats(ctypes.Structure):
+    _fields_ = [("casci", ctypes.c_int64), ("sigma_vectors", ctypes.c_int64),
+                ("sigma_flops", ctypes.c_double), ("iters_total", ctypes.c_int64),
+                ("iters_max", ctypes.c_int64), ("noconv", ctypes.c_int64)]
+
+
+def mbe_get_stats(ctx) -> dict:
+    s = mbe_stats()
+    L = load_library()
+    L.mbe_get_stats.argtypes = [ctypes.c_void_p, ctypes.POINTER(mbe_stats)]
+    _check(ctx, L.mbe_get_stats(ctx, ctypes.byref(s)))
+    return {k: getattr(s, k) for k, _ in mbe_stats._fields_}
+
+
+def mbe_reset_stats(ctx):
+    L = load_library()
+    L.mbe_reset_stats.argtypes = [ctypes.c_void_p]
+    _check(ctx, L.mbe_reset_stats(ctx))

@@ -1,0 +1,530 @@
+// CASCI building blocks of one bin of tuples (same active size n and same
+// number of active electrons per spin nsig):
+//   K1  string enumeration and the per-(string, orbital pair) link table
+//   K2  effective integrals of each tuple (inactive-core fold, Sec. 2/Fig. 2)
+//   K3  diagonal of H_active + shift * S^2 (Davidson preconditioner)
+//   K4  FP64 string-driven sigma vector: gather D, (kl|ij) contraction, pull
+//       scatter, plus the S^2 spin shift
+//
+// Sigma vector (Knowles & Handy, Chem. Phys. Lett. 111, 315 (1984); Olsen
+// et al., J. Chem. Phys. 89, 2185 (1988)): with h'_pq = h_pq - 1/2 sum_r
+// (pr|rq) and g'_{pq,rs} = (pq|rs) + (h'_pq d_rs + d_pq h'_rs)/N the active
+// Hamiltonian is H = 1/2 sum_{PQ} g'_{PQ} E+_P E+_Q over packed pairs
+// P = (p >= q), E+_P = E_pq + E_qp (E_pp on the diagonal).  Hence
+//   D_P(K)  = sum_J <K|E+_P|J> c_J            (gather)
+//   F_P(K)  = sum_Q g'_{PQ} D_Q(K)            (contraction)
+//   sigma_I = 1/2 sum_P sum_K <I|E+_P|K> F_P(K)   (pull scatter)
+// E+_P acting on one spin string has at most one non-zero matrix element
+// per string, which the link table stores.
+#include "mbe_internal.cuh"
+
+namespace {
+
+__constant__ int c_binom[33][33];
+
+bool g_binom_ready[64] = {false};
+
+void ensure_binom(int device) {
+  if (g_binom_ready[device]) return;
+  int tab[33][33];
+  for (int n = 0; n <= 32; n++)
+    for (int k = 0; k <= 32; k++) {
+      if (k == 0) tab[n][k] = 1;
+      else if (n == 0) tab[n][k] = 0;
+      else {
+        long long v = (long long)tab[n - 1][k - 1] + tab[n - 1][k];
+        tab[n][k] = v > 0x7fffffff ? 0x7fffffff : (int)v;
+      }
+    }
+  CU_CHECK(cudaMemcpyToSymbol(c_binom, tab, sizeof(tab)));
+  g_binom_ready[device] = true;
+}
+
+// colexicographic rank of a k-subset bit mask = its position when all
+// k-subsets are sorted by integer value
+__device__ __forceinline__ int mask_rank(uint32_t m) {
+  int r = 0, i = 1;
+  while (m) {
+    int p = __ffs(m) - 1;
+    r += c_binom[p][i];
+    i++;
+    m &= m - 1;
+  }
+  return r;
+}
+
+__device__ uint32_t mask_unrank(int r, int n, int k) {
+  uint32_t m = 0;
+  for (int i = k; i >= 1; i--) {
+    int p = i - 1;
+    while (p + 1 < n && c_binom[p + 1][i] <= r) p++;
+    m |= 1u << p;
+    r -= c_binom[p][i];
+  }
+  return m;
+}
+
+__global__ void k_strings(uint32_t* masks, int nstr, int n, int k) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I < nstr) masks[I] = mask_unrank(I, n, k);
+}
+
+__global__ void k_link(const uint32_t* masks, int32_t* link, int nstr, int n) {
+  int npair = n * (n + 1) / 2;
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nstr * npair) return;
+  int I = (int)(t / npair), P = (int)(t % npair);
+  int p = (int)((sqrtf(8.f * P + 1.f) - 1.f) * 0.5f);
+  while (p * (p + 1) / 2 > P) p--;
+  while ((p + 1) * (p + 2) / 2 <= P) p++;
+  int q = P - p * (p + 1) / 2;
+  uint32_t m = masks[I];
+  int32_t v = -1;
+  int bp = (m >> p) & 1, bq = (m >> q) & 1;
+  if (p == q) {
+    if (bp) v = I << 1;
+  } else if (bp != bq) {
+    uint32_t J = m ^ (1u << p) ^ (1u << q);
+    // orbitals strictly between q and p (p > q) decide the sign
+    uint32_t between = (m & ((1u << p) - 1u)) & ~((2u << q) - 1u);
+    int neg = __popc(between) & 1;
+    v = (mask_rank(J) << 1) | neg;
+  }
+  link[t] = v;
+}
+
+}  // namespace
+
+void build_string_tables(mbe_ctx* ctx, StringTables* t) {
+  ensure_binom(ctx->device);
+  long long nstr = 1;
+  for (int i = 0; i < t->nsig; i++) nstr = nstr * (t->n - i) / (i + 1);
+  if (nstr > (1 << 28)) throw MbeError{MBE_EINVAL, "string space too large"};
+  t->nstr = (int)nstr;
+  t->npair = t->n * (t->n + 1) / 2;
+  t->masks.reset(&ctx->pool, t->nstr);
+  t->link.reset(&ctx->pool, (size_t)t->nstr * t->npair);
+  k_strings<<<(t->nstr + 255) / 256, 256, 0, ctx->stream>>>(t->masks.ptr, t->nstr, t->n,
+                                                           t->nsig);
+  CU_LAUNCH_CHECK();
+  int64_t tot = (int64_t)t->nstr * t->npair;
+  k_link<<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(t->masks.ptr, t->link.ptr,
+                                                               t->nstr, t->n);
+  CU_LAUNCH_CHECK();
+}
+
+// ------------------------------------------------------------------ K2
+namespace {
+
+__device__ __forceinline__ int64_t gpair(int p, int q) {
+  return p >= q ? (int64_t)p * (p + 1) / 2 + q : (int64_t)q * (q + 1) / 2 + p;
+}
+
+// One CTA per tuple.  act: n sorted global orbital ids.
+__global__ void k_effints(const double* __restrict__ h, const double* __restrict__ eri,
+                          int norb, int nocc, int npair_g, const int32_t* __restrict__ act_all,
+                          int n, int nsig, double* ecore_out, double* heff_out, double* hp_out,
+                          double* gp_out, double* jk_out) {
+  const int b = blockIdx.x;
+  const int32_t* act = act_all + (int64_t)b * n;
+  extern __shared__ double sm[];
+  double* s_heff = sm;            // n*n
+  double* s_hp = sm + n * n;      // n*n
+  __shared__ int s_core[MBE_MAX_NORB];
+  __shared__ int s_ncore;
+  __shared__ int s_act[MBE_MAX_ACT];
+  if (threadIdx.x == 0) {
+    int nc = 0, j = 0;
+    for (int i = 0; i < nocc; i++) {
+      while (j < n && act[j] < i) j++;
+      if (!(j < n && act[j] == i)) s_core[nc++] = i;
+    }
+    s_ncore = nc;
+  }
+  if (threadIdx.x < n) s_act[threadIdx.x] = act[threadIdx.x];
+  __syncthreads();
+  const int nc = s_ncore;
+  const int64_t NP = npair_g;
+  // inactive-core energy (Fig. 2: occupied orbitals outside the active space
+  // stay doubly occupied): sum 2 h_ii + sum_ij [2 (ii|jj) - (ij|ji)]
+  if (threadIdx.x == 0) {
+    double e = 0.0;
+    for (int x = 0; x < nc; x++) {
+      int i = s_core[x];
+      e += 2.0 * h[(int64_t)i * norb + i];
+    }
+    double e2 = 0.0;
+    for (int x = 0; x < nc; x++)
+      for (int y = 0; y < nc; y++) {
+        int i = s_core[x], j = s_core[y];
+        e2 += 2.0 * eri[gpair(i, i) * NP + gpair(j, j)] - eri[gpair(i, j) * NP + gpair(j, i)];
+      }
+    ecore_out[b] = e + e2;
+  }
+  // h_eff_pq = h_pq + sum_i [2 (pq|ii) - (pi|iq)]
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    int p = t / n, q = t % n;
+    int P = s_act[p], Q = s_act[q];
+    double v = h[(int64_t)P * norb + Q];
+    for (int x = 0; x < nc; x++) {
+      int i = s_core[x];
+      v += 2.0 * eri[gpair(P, Q) * NP + gpair(i, i)] - eri[gpair(P, i) * NP + gpair(i, Q)];
+    }
+    s_heff[t] = v;
+    heff_out[(int64_t)b * n * n + t] = v;
+    jk_out[(int64_t)b * 2 * n * n + t] = eri[gpair(P, P) * NP + gpair(Q, Q)];
+    jk_out[(int64_t)b * 2 * n * n + n * n + t] = eri[gpair(P, Q) * NP + gpair(Q, P)];
+  }
+  __syncthreads();
+  // h'_pq = h_eff_pq - 1/2 sum_r (pr|rq), r over the active orbitals
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    int p = t / n, q = t % n;
+    int P = s_act[p], Q = s_act[q];
+    double v = 0.0;
+    for (int r = 0; r < n; r++) {
+      int R = s_act[r];
+      v += eri[gpair(P, R) * NP + gpair(R, Q)];
+    }
+    s_hp[t] = s_heff[t] - 0.5 * v;
+    hp_out[(int64_t)b * n * n + t] = s_hp[t];
+  }
+  __syncthreads();
+  // g'_{PQ} = (pq|rs) + (h'_pq d_rs + d_pq h'_rs) / N_active
+  const int npair = n * (n + 1) / 2;
+  const int nel = 2 * nsig;
+  const double inv = nel > 0 ? 1.0 / nel : 0.0;
+  for (int t = threadIdx.x; t < npair * npair; t += blockDim.x) {
+    int P = t / npair, Q = t % npair;
+    int p = (int)((sqrt(8.0 * P + 1.0) - 1.0) * 0.5);
+    while (p * (p + 1) / 2 > P) p--;
+    while ((p + 1) * (p + 2) / 2 <= P) p++;
+    int q = P - p * (p + 1) / 2;
+    int r = (int)((sqrt(8.0 * Q + 1.0) - 1.0) * 0.5);
+    while (r * (r + 1) / 2 > Q) r--;
+    while ((r + 1) * (r + 2) / 2 <= Q) r++;
+    int s = Q - r * (r + 1) / 2;
+    double v = eri[gpair(s_act[p], s_act[q]) * NP + gpair(s_act[r], s_act[s])];
+    if (r == s) v += s_hp[p * n + q] * inv;
+    if (p == q) v += s_hp[r * n + s] * inv;
+    gp_out[(int64_t)b * npair * npair + t] = v;
+  }
+}
+
+}  // namespace
+
+void launch_effints(mbe_ctx* ctx, BinProblem& bp) {
+  const int n = bp.n, B = bp.B;
+  bp.ecore.reset(&ctx->pool, B);
+  bp.heff.reset(&ctx->pool, (size_t)B * n * n);
+  bp.hp.reset(&ctx->pool, (size_t)B * n * n);
+  bp.gp.reset(&ctx->pool, (size_t)B * bp.npair * bp.npair);
+  bp.jk.reset(&ctx->pool, (size_t)B * 2 * n * n);
+  size_t smem = 2 * sizeof(double) * n * n;
+  k_effints<<<B, 256, smem, ctx->stream>>>(ctx->h.ptr, ctx->eri.ptr, ctx->norb, ctx->nocc,
+                                           ctx->npair_g, bp.act.ptr, n, bp.nsig, bp.ecore.ptr,
+                                           bp.heff.ptr, bp.hp.ptr, bp.gp.ptr, bp.jk.ptr);
+  CU_LAUNCH_CHECK();
+}
+
+// ------------------------------------------------------------------ K3
+namespace {
+
+// energy of one spin string with itself: sum h_pp + 1/2 sum_{pq} (J - K)
+__device__ __forceinline__ double string_self(uint32_t m, const double* heff, const double* J,
+                                              const double* K, int n) {
+  double e = 0.0, e2 = 0.0;
+  for (int p = 0; p < n; p++) {
+    if (!((m >> p) & 1)) continue;
+    e += heff[p * n + p];
+    for (int q = 0; q < n; q++)
+      if ((m >> q) & 1) e2 += J[p * n + q] - K[p * n + q];
+  }
+  return e + 0.5 * e2;
+}
+
+// <Ia Ib| H_active + shift S^2 |Ia Ib>, computed symmetrically in (Ia, Ib)
+__global__ void k_hdiag(const uint32_t* __restrict__ masks, int nstr, int n, int nsig,
+                        const double* __restrict__ heff_all, const double* __restrict__ jk_all,
+                        double shift, double* hd_all) {
+  const int b = blockIdx.y;
+  extern __shared__ double sm[];
+  double* s_heff = sm;
+  double* s_J = sm + n * n;
+  double* s_K = sm + 2 * n * n;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    s_heff[t] = heff_all[(int64_t)b * n * n + t];
+    s_J[t] = jk_all[(int64_t)b * 2 * n * n + t];
+    s_K[t] = jk_all[(int64_t)b * 2 * n * n + n * n + t];
+  }
+  __syncthreads();
+  const int64_t ndet = (int64_t)nstr * nstr;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndet;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int ia = (int)(i / nstr), ib = (int)(i % nstr);
+    uint32_t ma = masks[ia], mb = masks[ib];
+    double ea = string_self(ma, s_heff, s_J, s_K, n);
+    double eb = string_self(mb, s_heff, s_J, s_K, n);
+    double cross = 0.0;
+    for (int p = 0; p < n; p++) {
+      int ap = (ma >> p) & 1, bpp = (mb >> p) & 1;
+      if (ap & bpp) cross += s_J[p * n + p];
+      for (int q = 0; q < p; q++) {
+        int w = (ap & ((mb >> q) & 1)) + (((ma >> q) & 1) & bpp);
+        if (w) cross += w * s_J[p * n + q];
+      }
+    }
+    int ndocc = __popc(ma & mb);
+    hd_all[(int64_t)b * ndet + i] = (ea + eb) + cross + shift * (double)(nsig - ndocc);
+  }
+}
+
+}  // namespace
+
+void launch_hdiag(mbe_ctx* ctx, BinProblem& bp, double spin_shift, double* hd) {
+  const int n = bp.n;
+  size_t smem = 3 * sizeof(double) * n * n;
+  int64_t blocks = (bp.ndet + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  dim3 grid((unsigned)blocks, bp.B);
+  k_hdiag<<<grid, 256, smem, ctx->stream>>>(bp.tab->masks.ptr, bp.nstr, n, bp.nsig,
+                                            bp.heff.ptr, bp.jk.ptr, spin_shift, hd);
+  CU_LAUNCH_CHECK();
+}
+
+// ------------------------------------------------------------------ K4
+namespace {
+
+// D[b][P][Ia*nstr+Ib] = s_a C(Ja, Ib) + s_b C(Ia, Jb)
+__global__ void k_gather_fp64(const int32_t* __restrict__ link, int nstr, int npair,
+                              const double* __restrict__ c, int64_t c_stride,
+                              const int32_t* __restrict__ active, const int32_t* __restrict__ bmap,
+                              double* __restrict__ D) {
+  const int bl = blockIdx.y;                 // local index in the sub-batch
+  const int b = bmap[bl];
+  if (active && !active[b]) return;
+  const double* cb = c + (int64_t)b * c_stride;
+  const int64_t ndet = (int64_t)nstr * nstr;
+  double* Db = D + (int64_t)bl * npair * ndet;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndet;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int ia = (int)(i / nstr), ib = (int)(i % nstr);
+    const int32_t* la = link + (int64_t)ia * npair;
+    const int32_t* lb = link + (int64_t)ib * npair;
+    for (int P = 0; P < npair; P++) {
+      double v = 0.0;
+      int32_t ta = la[P], tb = lb[P];
+      if (ta >= 0) {
+        double x = cb[(int64_t)(ta >> 1) * nstr + ib];
+        v += (ta & 1) ? -x : x;
+      }
+      if (tb >= 0) {
+        double x = cb[(int64_t)ia * nstr + (tb >> 1)];
+        v += (tb & 1) ? -x : x;
+      }
+      Db[(int64_t)P * ndet + i] = v;
+    }
+  }
+}
+
+// E[b][P][k] = sum_Q g'[b][P][Q] D[b][Q][k]: FP64 tiles of all rows x 64 columns
+constexpr int GT_N = 64;
+__global__ void __launch_bounds__(256) k_contract_fp64(const double* __restrict__ gp_all, int npair,
+                                                       const double* __restrict__ D, int64_t ndet,
+                                                       const int32_t* __restrict__ active,
+                                                       const int32_t* __restrict__ bmap,
+                                                       double* __restrict__ E) {
+  const int bl = blockIdx.y;
+  const int b = bmap[bl];
+  if (active && !active[b]) return;
+  extern __shared__ double sm[];
+  double* s_g = sm;                          // npair * npair
+  double* s_d = sm + npair * npair;          // npair * GT_N
+  const double* g = gp_all + (int64_t)b * npair * npair;
+  for (int t = threadIdx.x; t < npair * npair; t += blockDim.x) s_g[t] = g[t];
+  const double* Db = D + (int64_t)bl * npair * ndet;
+  double* Eb = E + (int64_t)bl * npair * ndet;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  for (int64_t col0 = (int64_t)blockIdx.x * GT_N; col0 < ndet; col0 += (int64_t)gridDim.x * GT_N) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < npair * GT_N; t += blockDim.x) {
+      int k = t / GT_N, j = t % GT_N;
+      int64_t col = col0 + j;
+      s_d[t] = col < ndet ? Db[(int64_t)k * ndet + col] : 0.0;
+    }
+    __syncthreads();
+    for (int r0 = 0; r0 < npair; r0 += 16 * 8) {
+      double acc[8][4];
+#pragma unroll
+      for (int i = 0; i < 8; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
+      for (int k = 0; k < npair; k++) {
+        double dv[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) dv[j] = s_d[k * GT_N + tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+          int r = r0 + ty + 16 * i;
+          double gv = r < npair ? s_g[r * npair + k] : 0.0;
+#pragma unroll
+          for (int j = 0; j < 4; j++) acc[i][j] = fma(gv, dv[j], acc[i][j]);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 8; i++) {
+        int r = r0 + ty + 16 * i;
+        if (r >= npair) continue;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          int64_t col = col0 + tx + 16 * j;
+          if (col < ndet) Eb[(int64_t)r * ndet + col] = acc[i][j];
+        }
+      }
+    }
+  }
+}
+
+// sigma(Ia,Ib) = 1/2 sum_P [s_a E_P(Ja,Ib) + s_b E_P(Ia,Jb)] + shift (S^2 c)(Ia,Ib)
+// S^2 c = (nsig - ndocc) c - sum over pairs {p,q} with Ia holding one of them
+// and Ib the other of s_a s_b c(Ja, Jb)   (S^2 = N_beta - sum E^a_qp E^b_pq)
+__global__ void k_scatter_fp64(const int32_t* __restrict__ link, const uint32_t* __restrict__ masks,
+                               int nstr, int n, int nsig, const double* __restrict__ E,
+                               const double* __restrict__ c, int64_t c_stride, double shift,
+                               const int32_t* __restrict__ active, const int32_t* __restrict__ bmap,
+                               double* __restrict__ out, int64_t out_stride) {
+  const int bl = blockIdx.y;
+  const int b = bmap[bl];
+  if (active && !active[b]) return;
+  const int npair = n * (n + 1) / 2;
+  const int64_t ndet = (int64_t)nstr * nstr;
+  const double* Eb = E + (int64_t)bl * npair * ndet;
+  const double* cb = c + (int64_t)b * c_stride;
+  double* ob = out + (int64_t)b * out_stride;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndet;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int ia = (int)(i / nstr), ib = (int)(i % nstr);
+    const int32_t* la = link + (int64_t)ia * npair;
+    const int32_t* lb = link + (int64_t)ib * npair;
+    double acc = 0.0;
+    for (int P = 0; P < npair; P++) {
+      int32_t ta = la[P], tb = lb[P];
+      if (ta >= 0) {
+        double x = Eb[(int64_t)P * ndet + (int64_t)(ta >> 1) * nstr + ib];
+        acc += (ta & 1) ? -x : x;
+      }
+      if (tb >= 0) {
+        double x = Eb[(int64_t)P * ndet + (int64_t)ia * nstr + (tb >> 1)];
+        acc += (tb & 1) ? -x : x;
+      }
+    }
+    double v = 0.5 * acc;
+    if (shift != 0.0) {
+      uint32_t ma = masks[ia], mb = masks[ib];
+      double s2 = (double)(nsig - __popc(ma & mb)) * cb[i];
+      uint32_t oa = ma & ~mb, ob2 = mb & ~ma;   // open shells of each spin
+      for (int q = 0; q < n; q++) {
+        if (!((oa >> q) & 1)) continue;
+        for (int p = 0; p < n; p++) {
+          if (!((ob2 >> p) & 1)) continue;
+          int P = p > q ? p * (p + 1) / 2 + q : q * (q + 1) / 2 + p;
+          int32_t ta = la[P], tb = lb[P];
+          double x = cb[(int64_t)(ta >> 1) * nstr + (tb >> 1)];
+          s2 -= ((ta ^ tb) & 1) ? -x : x;
+        }
+      }
+      v += shift * s2;
+    }
+    ob[i] = v;
+  }
+}
+
+__global__ void k_s2(const int32_t* __restrict__ link, const uint32_t* __restrict__ masks,
+                     int nstr, int n, int nsig, const double* __restrict__ c, int64_t c_stride,
+                     const int32_t* __restrict__ active, double* __restrict__ out,
+                     int64_t out_stride) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const int npair = n * (n + 1) / 2;
+  const int64_t ndet = (int64_t)nstr * nstr;
+  const double* cb = c + (int64_t)b * c_stride;
+  double* ob = out + (int64_t)b * out_stride;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndet;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int ia = (int)(i / nstr), ib = (int)(i % nstr);
+    const int32_t* la = link + (int64_t)ia * npair;
+    const int32_t* lb = link + (int64_t)ib * npair;
+    uint32_t ma = masks[ia], mb = masks[ib];
+    double s2 = (double)(nsig - __popc(ma & mb)) * cb[i];
+    uint32_t oa = ma & ~mb, obm = mb & ~ma;
+    for (int q = 0; q < n; q++) {
+      if (!((oa >> q) & 1)) continue;
+      for (int p = 0; p < n; p++) {
+        if (!((obm >> p) & 1)) continue;
+        int P = p > q ? p * (p + 1) / 2 + q : q * (q + 1) / 2 + p;
+        int32_t ta = la[P], tb = lb[P];
+        double x = cb[(int64_t)(ta >> 1) * nstr + (tb >> 1)];
+        s2 -= ((ta ^ tb) & 1) ? -x : x;
+      }
+    }
+    ob[i] = s2;
+  }
+}
+
+}  // namespace
+
+void sigma_fp64(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const double* c, int64_t c_stride,
+                double* out, int64_t out_stride, const int32_t* active, double spin_shift) {
+  const int npair = bp.npair;
+  const int64_t ndet = bp.ndet;
+  // sub-batch so that D and E stay within ~2 GB each
+  int64_t per = (int64_t)npair * ndet;
+  int64_t sb = (int64_t)(2.0e9 / 8.0) / (per > 0 ? per : 1);
+  if (sb < 1) sb = 1;
+  if (sb > bp.B) sb = bp.B;
+  if (w.sub_batch != sb || w.D.n < (size_t)(sb * per)) {
+    w.D.reset(&ctx->pool, sb * per);
+    w.E.reset(&ctx->pool, sb * per);
+    w.sub_batch = sb;
+  }
+  std::vector<int32_t> bm(bp.B);
+  for (int i = 0; i < bp.B; i++) bm[i] = i;
+  DevBuf<int32_t> bmap(&ctx->pool, bp.B);
+  CU_CHECK(cudaMemcpyAsync(bmap.ptr, bm.data(), sizeof(int32_t) * bp.B, cudaMemcpyHostToDevice,
+                           ctx->stream));
+  int64_t blocks = (ndet + 255) / 256;
+  if (blocks > 2048) blocks = 2048;
+  size_t smem_c = sizeof(double) * (npair * npair + npair * GT_N);
+  static bool attr_set = false;
+  if (!attr_set) {
+    CU_CHECK(cudaFuncSetAttribute(k_contract_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  200 * 1024));
+    attr_set = true;
+  }
+  int64_t cblocks = (ndet + GT_N - 1) / GT_N;
+  if (cblocks > 1024) cblocks = 1024;
+  for (int64_t b0 = 0; b0 < bp.B; b0 += sb) {
+    int nb = (int)std::min<int64_t>(sb, bp.B - b0);
+    dim3 g1((unsigned)blocks, nb);
+    k_gather_fp64<<<g1, 256, 0, ctx->stream>>>(bp.tab->link.ptr, bp.nstr, npair, c, c_stride,
+                                               active, bmap.ptr + b0, w.D.ptr);
+    CU_LAUNCH_CHECK();
+    dim3 g2((unsigned)cblocks, nb);
+    k_contract_fp64<<<g2, 256, smem_c, ctx->stream>>>(bp.gp.ptr, npair, w.D.ptr, ndet, active,
+                                                      bmap.ptr + b0, w.E.ptr);
+    CU_LAUNCH_CHECK();
+    k_scatter_fp64<<<g1, 256, 0, ctx->stream>>>(bp.tab->link.ptr, bp.tab->masks.ptr, bp.nstr,
+                                                bp.n, bp.nsig, w.E.ptr, c, c_stride, spin_shift,
+                                                active, bmap.ptr + b0, out, out_stride);
+    CU_LAUNCH_CHECK();
+  }
+}
+
+void s2_apply(mbe_ctx* ctx, BinProblem& bp, const double* c, int64_t c_stride, double* out,
+              int64_t out_stride, const int32_t* active) {
+  int64_t blocks = (bp.ndet + 255) / 256;
+  if (blocks > 2048) blocks = 2048;
+  dim3 g((unsigned)blocks, bp.B);
+  k_s2<<<g, 256, 0, ctx->stream>>>(bp.tab->link.ptr, bp.tab->masks.ptr, bp.nstr, bp.n, bp.nsig, c,
+                                   c_stride, active, out, out_stride);
+  CU_LAUNCH_CHECK();
+}

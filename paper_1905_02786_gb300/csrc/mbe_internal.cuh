@@ -1,0 +1,193 @@
+// Internal declarations shared by the CUDA translation units of libmbe.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+#include <map>
+#include <unordered_map>
+#include "../../include/mbe.h"
+
+#define MBE_MAX_ACT 30      // active orbitals per CASCI (string masks are uint32)
+#define MBE_MAX_NORB 128    // tuple keys are 128-bit orbital sets
+#define MBE_MAX_ORDER 16    // increments enumerate 2^order - 2 subtuples
+
+// ---------------------------------------------------------------- errors
+struct MbeError {
+  int code;
+  std::string msg;
+};
+
+#define CU_CHECK(call)                                                      \
+  do {                                                                      \
+    cudaError_t e_ = (call);                                                \
+    if (e_ != cudaSuccess)                                                  \
+      throw MbeError{MBE_ECUDA, std::string(#call) + ": " +                 \
+                                    cudaGetErrorString(e_)};                \
+  } while (0)
+
+#define CU_LAUNCH_CHECK() CU_CHECK(cudaGetLastError())
+
+// --------------------------------------------------------- device memory
+// A caching allocator: freed blocks are kept per size and reused; the total
+// held by the context is capped by mem_cap (0 = no cap).
+struct DevPool {
+  int64_t cap = 0, held = 0;
+  std::multimap<size_t, void*> free_blocks;
+  std::unordered_map<void*, size_t> sizes;
+  void* alloc(size_t bytes);
+  void release(void* p);
+  void trim();
+  ~DevPool();
+};
+
+template <typename T>
+struct DevBuf {
+  DevPool* pool = nullptr;
+  T* ptr = nullptr;
+  size_t n = 0;
+  DevBuf() {}
+  DevBuf(DevPool* p, size_t count) { reset(p, count); }
+  void reset(DevPool* p, size_t count) {
+    release();
+    pool = p;
+    n = count;
+    ptr = count ? (T*)p->alloc(count * sizeof(T)) : nullptr;
+  }
+  void release() {
+    if (ptr && pool) pool->release(ptr);
+    ptr = nullptr;
+    n = 0;
+  }
+  ~DevBuf() { release(); }
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+};
+
+// --------------------------------------------------------- string tables
+// Strings of nsig electrons in n active orbitals, ordered by the integer
+// value of their occupation bit mask (colexicographic rank).  For every
+// string I and packed orbital pair P = (p >= q) the table holds the unique
+// string J with <I| E_pq + E_qp |J> != 0 (E_pp for p == q) and its sign,
+// packed as (J << 1) | (sign < 0), or -1 if there is none.
+struct StringTables {
+  int n = 0, nsig = 0, nstr = 0, npair = 0;
+  DevBuf<uint32_t> masks;  // nstr
+  DevBuf<int32_t> link;    // nstr * npair
+};
+
+// ------------------------------------------------------------- context
+struct KeptCI {
+  int order;
+  std::vector<int32_t> tuple;  // global orbital ids of the tuple
+  int n, nsig;
+  std::vector<double> c;       // converged CI vector (nstr*nstr), host copy
+};
+
+struct HashTable {
+  int64_t cap = 0;             // power of two
+  int64_t count = 0;
+  DevBuf<unsigned long long> keys;  // 2 words per slot
+  DevBuf<double> val;          // increment
+  DevBuf<uint8_t> keep;        // screening flag
+  DevBuf<int32_t> state;       // 0 empty, 1 claimed/filled
+};
+
+struct OrderRec {
+  int order;
+  std::vector<int32_t> tuples;   // ntup * order
+  std::vector<double> eps, inc;
+  std::vector<uint8_t> keep;
+};
+
+struct mbe_ctx {
+  int device = 0;
+  mbe_stats stats = {};
+  mbe_options opt;
+  cudaStream_t stream = nullptr;
+  std::string last_error;
+  DevPool pool;
+
+  // integrals
+  int norb = 0, nelec = 0, nocc = 0, npair_g = 0;
+  DevBuf<double> h, eri;
+  std::vector<double> h_host, eri_host;
+
+  // reference / expansion space
+  std::vector<int> ref, exp;
+  bool have_ref = false;
+  double e_ref = 0.0;
+
+  // string tables per (n, nsig)
+  std::map<std::pair<int, int>, StringTables*> tables;
+
+  // MBE state
+  HashTable hash;
+  int last_order = 0;                 // highest order with increments
+  int cur_order = 0;                  // order of the last solved tuples
+  std::vector<int32_t> cur_tuples;    // ntup * cur_order (host)
+  std::vector<double> cur_eps;
+  DevBuf<int32_t> cur_tuples_dev;
+  DevBuf<double> cur_eps_dev;
+  std::vector<int32_t> prev_tuples;   // last processed order (host)
+  std::vector<uint8_t> prev_keep;
+  int prev_order = 0;
+  std::vector<double> order_sums;
+  std::vector<OrderRec> history;      // every processed order
+  // all processed tuples (for the backward): order, tuple, kept CI
+  std::vector<KeptCI> kept;
+  bool kept_ref = false;
+  KeptCI ref_ci;
+
+  ~mbe_ctx();
+};
+
+// ------------------------------------------------- per-bin solver state
+struct BinProblem {
+  int n, nsig, nstr, npair;
+  int64_t ndet;
+  int B;                         // tuples in this batch
+  const StringTables* tab;
+  DevBuf<int32_t> act;           // B * n global orbital ids
+  DevBuf<double> ecore;          // B
+  DevBuf<double> heff;           // B * n * n
+  DevBuf<double> hp;             // B * n * n   (h' = heff - 1/2 sum_r (pr|rq))
+  DevBuf<double> gp;             // B * npair * npair
+  DevBuf<double> jk;             // B * 2 * n * n  (J_pq = (pp|qq), K_pq = (pq|qp))
+};
+
+// ------------------------------------------------------------ launchers
+void build_string_tables(mbe_ctx* ctx, StringTables* t);
+void launch_effints(mbe_ctx* ctx, BinProblem& bp);
+void launch_hdiag(mbe_ctx* ctx, BinProblem& bp, double spin_shift, double* hd);
+
+// sigma for a batch: out[b] = (H_act + shift S^2) c[b] for b < B; c/out with
+// strides (elements between consecutive tuples' vectors); active may be NULL.
+struct SigmaWork {
+  DevBuf<double> D, E;           // scratch for the FP64 path
+  DevBuf<float> Df;              // scratch for the mixed path
+  int64_t sub_batch = 0;
+};
+void sigma_fp64(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const double* c,
+                int64_t c_stride, double* out, int64_t out_stride,
+                const int32_t* active, double spin_shift);
+void s2_apply(mbe_ctx* ctx, BinProblem& bp, const double* c, int64_t c_stride,
+              double* out, int64_t out_stride, const int32_t* active);
+
+// Davidson for a batch; writes e_out (B, total energies incl. core),
+// status (B), s2 (B), and, if x_out != NULL, the converged vectors (B*ndet).
+void davidson_batch(mbe_ctx* ctx, BinProblem& bp, double* e_out_host,
+                    int32_t* status_host, double* s2_host, double* x_out_dev);
+
+// hash / increments
+void hash_init(mbe_ctx* ctx, int64_t cap);
+void hash_insert(mbe_ctx* ctx, const int32_t* tuples_dev, int order, int64_t ntup,
+                 const double* vals_dev, const uint8_t* keep_dev);
+void increments_kernel_launch(mbe_ctx* ctx, const int32_t* tuples_dev, int order,
+                              int64_t ntup, const double* eps_dev, double eps_ref,
+                              double thr, double* inc_dev, uint8_t* keep_dev,
+                              int32_t* err_dev);
+double kahan_sum_device(mbe_ctx* ctx, const double* v, int64_t n);
+int64_t next_tuples_device(mbe_ctx* ctx, const int32_t* parents_dev, int order_prev,
+                           int64_t nparents, const int32_t* exp_dev, int nexp,
+                           DevBuf<int32_t>& out);
