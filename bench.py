@@ -1,0 +1,319 @@
+"""Benchmark of the MBE-FCI hot path on GB300.
+
+One step = one complete many-body expansion of the workload (default: the
+8e/23o water-double-zeta-shaped system, CAS(6e,6o) reference, 17 expansion
+orbitals to order 6, screening 1e-6 Eh): tuple generation, every CASCI
+(effective integrals, string tables, diagonal, Davidson with the
+string-driven sigma), increment assembly by hash lookup, screening and
+Kahan order sums, all through the C ABI of include/mbe.h.
+
+Metric: CASCI increments per second (tuples solved and assembled per second)
+over the whole job.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+  python bench.py --impl reference ...   # the CPU oracle on a bounded sample
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import mbe_synth as ms  # noqa: E402
+
+METRIC = ("CASCI increments/sec and sigma TFLOP/s, mixed+batched vs plain FP64 GPU "
+          "at 1e-7 Eh")
+UNIT = "increments/s"
+DEFAULT_WORKLOAD = "h2o_dz_8e23o"
+
+# DRAM traffic per launch of the dominant kernel from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by kernel; valid only
+# while the kernel source is unchanged (sha256 of the source file).
+TRAFFIC = {}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def src_sha(path):
+    return hashlib.sha256(open(os.path.join(ROOT, path), "rb").read()).hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample_rate(w, h, eri, ntup_per_order=2, orders=(1, 2, 3), seed=7):
+    """The oracle (as it stands) on a seeded sample of the workload's tuples:
+    returns (tuples/s, seconds, description, cores)."""
+    from oracle import casci as oc
+    from oracle import mbe as om
+    cores = len(os.sched_getaffinity(0))
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    sample = []
+    for k in orders:
+        sample += ms.sample_tuples(w["exp"], k, ntup_per_order, seed + k)
+    t0 = time.perf_counter()
+    for t in sample:
+        oc.casci(h, eri, w["nocc"], om.active_space(w["ref"], t))
+    dt = time.perf_counter() - t0
+    desc = (f"{len(sample)} seeded random tuples ({ntup_per_order} each of orders "
+            f"{list(orders)}) of {w['name']}, each CASCI solved by the oracle; higher orders "
+            f"are larger, so the oracle's rate on the full expansion is lower")
+    return len(sample) / dt, dt, desc, cores
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = ms.workload(args.workload)
+    h, eri, _ = ms.workload_integrals(args.workload)
+    for _ in range(args.warmup):
+        oracle_sample_rate(w, h, eri, ntup_per_order=1, orders=(1,))
+    tot_t, tot_n, desc, cores = 0.0, 0, "", 1
+    for s in range(args.steps):
+        rate, dt, desc, cores = oracle_sample_rate(w, h, eri, ntup_per_order=1,
+                                                   orders=(1, 2, 3), seed=100 + s)
+        tot_t += dt
+        tot_n += int(round(rate * dt))
+    value = tot_n / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot_t / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "sample": desc},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def transfer_bytes(res, h, eri):
+    """Bytes that cross the C ABI per expansion: tuples out of next_tuples,
+    tuples into solve, energies/status/increments/keep back."""
+    h2d = d2h = 0
+    for o in res["orders"]:
+        n, k = o["tuples"].shape
+        d2h += 4 * n * k          # mbe_next_tuples
+        h2d += 4 * n * k          # mbe_solve_tuples input
+        d2h += 8 * n + 4 * n      # energies + status
+        d2h += 8 * n + n + 16     # increments + keep + sums
+    return h2d, d2h
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["mixed", "fp64"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--max-order", type=int, default=None)
+    ap.add_argument("--max-batch", type=int, default=4096)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1905_02786_gb300 import build, _binding as B, driver
+    build.build()
+    B.load_library()
+
+    w = ms.workload(args.workload)
+    h, eri, _ = ms.workload_integrals(args.workload)
+    max_order = args.max_order or w["max_order"]
+    prec = B.MBE_MIXED_BF16X3 if args.precision == "mixed" else B.MBE_FP64
+    m = B.MBE(local, precision=prec, max_batch=args.max_batch, timing=1)
+    stream = torch.cuda.Stream()
+    B.mbe_set_stream(m.ctx, stream.cuda_stream)
+    m.load(h, eri, w["nel"])
+    allgather = driver.torch_allgather() if world > 1 else None
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        return driver.run_expansion(m.ctx, w["ref"], w["exp"], max_order, w["thr"], rank, world,
+                                    allgather)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        res = step()
+    # timed region: K expansions; L2 flushed before each (on the same stream)
+    B.mbe_reset_stats(m.ctx)
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ntup = 0
+    flush_ms = 0.0
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for _ in range(args.steps):
+            fa, fb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            fa.record(stream)
+            flush.fill_(1.0)
+            fb.record(stream)
+            res = step()
+            ntup += res["ntup"]
+            fb.synchronize()
+            flush_ms += fa.elapsed_time(fb)
+        ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    t_ms = ev0.elapsed_time(ev1) - flush_ms
+    if world > 1:
+        t = torch.tensor([t_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_ms = float(t.item())
+    st = B.mbe_get_stats(m.ctx)
+    value = ntup / (t_ms / 1e3)
+
+    # end to end through the C ABI with host buffers: integrals uploaded and
+    # every per-order array copied inside the timed region
+    barrier()
+    e0 = time.perf_counter()
+    for _ in range(args.steps):
+        m.load(h, eri, w["nel"])
+        r2 = step()
+    barrier()
+    e_dt = time.perf_counter() - e0
+    h2d, d2h = transfer_bytes(r2, h, eri)
+    h2d += h.nbytes + eri.nbytes
+    e2e = {"value": args.steps * r2["ntup"] / e_dt, "unit": UNIT,
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    pk, pk_kind = peaks()
+    dom_ms_per = st["dom_ms"] / max(st["dom_launches"], 1)
+    dom_flops_per = st["dom_flops"] / max(st["dom_launches"], 1)
+    achieved_tf = dom_flops_per / (dom_ms_per * 1e-3) / 1e12 if dom_ms_per > 0 else None
+    if prec == B.MBE_FP64:
+        kname = "k_contract_fp64"
+        peak_tf, peak_src = 1.25, "nominal GB300 FP64 1.25 TFLOP/s (no measured FP64 peak)"
+        bound = "alu"
+        ksrc = "paper_1905_02786_gb300/csrc/mbe_ci.cu"
+    else:
+        kname = "k_sigma_tc"
+        peak_tf = pk.get("bf16_tflops_sustained", 1700.0)
+        peak_src = f"bf16 dense sustained, {pk_kind}"
+        bound = "tensor"
+        ksrc = "paper_1905_02786_gb300/csrc/mbe_sigma_tc.cu"
+    tr = TRAFFIC.get(kname)
+    traffic = tr["bytes"] if tr and tr["sha"] == src_sha(ksrc) else None
+    roofline = {"bound": bound, "kernel": kname, "achieved": achieved_tf, "peak": peak_tf,
+                "unit": "TFLOP/s", "frac": (achieved_tf / peak_tf) if achieved_tf else None,
+                "traffic": traffic, "peak_source": peak_src,
+                "flops_per_launch": dom_flops_per, "ms_per_launch": dom_ms_per,
+                "launches": st["dom_launches"]}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, dt, desc, cores = oracle_sample_rate(w, h, eri)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+               "seconds": dt}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+                "scaling": "strong", "vs_baseline": None,
+                "dtype": "f64" if prec == B.MBE_FP64 else "bf16x3(f32 acc)+f64",
+                "data": "synthetic",
+                "config": {"workload": args.workload, "norb": w["norb"], "nelec": w["nel"],
+                           "reference": f"CAS({2 * sum(1 for r in w['ref'] if r < w['nocc'])}e,"
+                                        f"{len(w['ref'])}o)",
+                           "expansion_orbitals": len(w["exp"]), "max_order": max_order,
+                           "screen_thr": w["thr"], "precision": args.precision,
+                           "tuples_per_step": ntup // args.steps,
+                           "l2": "256 MiB buffer written before each step (flushed); "
+                                 "Davidson working set exceeds L2",
+                           "parallelism": f"tuple-sharded x{world}" if world > 1 else "1 GPU"},
+                "sigma_tflops": (st["sigma_flops"] / (st["dom_ms"] * 1e-3) / 1e12)
+                if st["dom_ms"] else None,
+                "davidson_iters_mean": st["iters_total"] / max(st["casci"], 1),
+                "noconv": st["noconv"],
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(st["launches"]), "clocks": clk,
+                "total_energy": res["total"]}
+        print(json.dumps(line), flush=True)
+    m.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

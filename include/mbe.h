@@ -77,6 +77,8 @@ typedef struct mbe_options {
   int deterministic;    /* 1: fixed-order reductions only (no float atomics) */
   int64_t mem_cap_bytes;/* cap on device memory the context may allocate; 0 =
                            no cap (exceeding it returns MBE_ENOMEM)          */
+  int timing;           /* 1: time the sigma contraction launches with CUDA
+                           events (mbe_stats.dom_ms)                         */
 } mbe_options;
 
 typedef struct mbe_ctx mbe_ctx;
@@ -90,6 +92,12 @@ typedef struct mbe_stats {
   int64_t iters_total;    /* Davidson iterations summed over CASCIs           */
   int64_t iters_max;      /* largest iteration count of one CASCI             */
   int64_t noconv;         /* CASCIs that hit the iteration cap                */
+  int64_t launches;       /* kernel launches issued by the library            */
+  int64_t dom_launches;   /* launches of the sigma contraction kernel (FP64
+                             contraction, or the fused tensor-core sigma)     */
+  double dom_ms;          /* their summed device time (CUDA events on the
+                             context stream); 0 unless opt.timing = 1         */
+  double dom_flops;       /* their algorithmic flops, 2 N_det npair^2 each   */
 } mbe_stats;
 
 /* Fill *opt with the defaults (FP64, max_batch 256, subspace 16, 200
@@ -101,6 +109,12 @@ void mbe_default_options(mbe_options* opt);
  * The context owns its device memory and a CUDA stream. */
 int mbe_create(mbe_ctx** out, int device, const mbe_options* opt);
 void mbe_destroy(mbe_ctx* ctx);
+
+/* Make the context issue its work on `stream` (a cudaStream_t of the
+ * context's device, caller-owned, must outlive its use); NULL restores the
+ * context's own stream.  Lets a caller bracket the library's work with CUDA
+ * events on a stream it knows. */
+int mbe_set_stream(mbe_ctx* ctx, void* stream);
 const char* mbe_last_error(const mbe_ctx* ctx);
 
 /* Load the molecular integrals (input of every CASCI of Sec. 2).
@@ -164,6 +178,16 @@ int mbe_next_tuples(mbe_ctx* ctx, int order, int32_t* tuples_out, int64_t cap,
  *  deri   npair*npair, gradient w.r.t. the symmetric packed eri matrix
  *         (sum over the full-tensor images of (P,Q), symmetrised P<->Q). */
 int mbe_energy_backward(mbe_ctx* ctx, double scale, double* dh, double* deri);
+
+/* Make `tuples` (ntup rows of `order` orbitals, ascending) with the given
+ * CASCI energies eps (total, Eh) the current order, as mbe_solve_tuples
+ * would, without solving.  Used when the tuples of one order are solved on
+ * several GPUs: each process solves its share, the energies are gathered
+ * and every process continues with mbe_increments on the full order.
+ * Kept CI vectors (keep_ci) of tuples this context solved for this order
+ * are retained. */
+int mbe_set_order_energies(mbe_ctx* ctx, int order, const int32_t* tuples,
+                           int64_t ntup, const double* eps);
 
 /* Copy the context's counters to *out (host). */
 int mbe_get_stats(const mbe_ctx* ctx, mbe_stats* out);

@@ -24,7 +24,7 @@ ERROR_NAMES = {0: "MBE_OK", -1: "MBE_EINVAL", -2: "MBE_ENOMEM", -3: "MBE_ECUDA",
 EXPORTED = ["mbe_default_options", "mbe_create", "mbe_destroy", "mbe_last_error",
             "mbe_load_integrals", "mbe_set_reference", "mbe_solve_tuples",
             "mbe_increments", "mbe_next_tuples", "mbe_energy_backward", "mbe_sigma",
-            "mbe_get_stats", "mbe_reset_stats"]
+            "mbe_get_stats", "mbe_reset_stats", "mbe_set_order_energies", "mbe_set_stream"]
 
 
 class MBEError(RuntimeError):
@@ -38,7 +38,8 @@ class mbe_options(ctypes.Structure):
                 ("max_subspace", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("conv_tol_r", ctypes.c_double), ("conv_tol_e", ctypes.c_double),
                 ("spin_shift", ctypes.c_double), ("keep_ci", ctypes.c_int),
-                ("deterministic", ctypes.c_int), ("mem_cap_bytes", ctypes.c_int64)]
+                ("deterministic", ctypes.c_int), ("mem_cap_bytes", ctypes.c_int64),
+                ("timing", ctypes.c_int)]
 
 
 _lib = None
@@ -70,7 +71,8 @@ def load_library(path: str = LIB_PATH):
     L.mbe_sigma.argtypes = [vp, vp, c_int, vp, vp, vp]
     for name in EXPORTED:
         if name not in ("mbe_default_options", "mbe_destroy", "mbe_last_error",
-                        "mbe_get_stats", "mbe_reset_stats"):
+                        "mbe_get_stats", "mbe_reset_stats", "mbe_set_order_energies",
+                        "mbe_set_stream"):
             getattr(L, name).restype = c_int
     _lib = L
     return L
@@ -223,7 +225,20 @@ class MBE:
 class mbe_stats(ctypes.Structure):
     _fields_ = [("casci", ctypes.c_int64), ("sigma_vectors", ctypes.c_int64),
                 ("sigma_flops", ctypes.c_double), ("iters_total", ctypes.c_int64),
-                ("iters_max", ctypes.c_int64), ("noconv", ctypes.c_int64)]
+                ("iters_max", ctypes.c_int64), ("noconv", ctypes.c_int64),
+                ("launches", ctypes.c_int64), ("dom_launches", ctypes.c_int64),
+                ("dom_ms", ctypes.c_double), ("dom_flops", ctypes.c_double)]
+
+
+def mbe_set_order_energies(ctx, tuples, eps, order: int | None = None):
+    t = np.ascontiguousarray(tuples, dtype=np.int32)
+    if t.ndim == 1:
+        t = t.reshape(-1, order or 1)
+    e = np.ascontiguousarray(eps, dtype=np.float64)
+    L = load_library()
+    L.mbe_set_order_energies.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                         ctypes.c_int64, ctypes.c_void_p]
+    _check(ctx, L.mbe_set_order_energies(ctx, order or t.shape[1], _p(t), t.shape[0], _p(e)))
 
 
 def mbe_get_stats(ctx) -> dict:
@@ -238,3 +253,11 @@ def mbe_reset_stats(ctx):
     L = load_library()
     L.mbe_reset_stats.argtypes = [ctypes.c_void_p]
     _check(ctx, L.mbe_reset_stats(ctx))
+
+
+def mbe_set_stream(ctx, stream_handle):
+    """Issue the context's work on a caller-owned cudaStream_t (an int handle,
+    e.g. torch.cuda.Stream().cuda_stream); 0/None restores its own stream."""
+    L = load_library()
+    L.mbe_set_stream.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    _check(ctx, L.mbe_set_stream(ctx, ctypes.c_void_p(stream_handle or None)))

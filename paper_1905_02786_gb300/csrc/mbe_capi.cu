@@ -6,6 +6,8 @@
 #include <cstring>
 #include <set>
 
+int64_t g_mbe_launches = 0;
+
 // ------------------------------------------------------------ DevPool
 void* DevPool::alloc(size_t bytes) {
   if (bytes == 0) return nullptr;
@@ -113,13 +115,6 @@ int count_sig(const mbe_ctx* ctx, const std::vector<int>& act) {
   return s;
 }
 
-int64_t binom64(int n, int k) {
-  if (k < 0 || k > n) return 0;
-  int64_t r = 1;
-  for (int i = 0; i < k; i++) r = r * (n - i) / (i + 1);
-  return r;
-}
-
 // Solve the CASCI of every active space in `acts`; binned by (n, nsig).
 void solve_jobs(mbe_ctx* ctx, const std::vector<std::vector<int>>& acts, double* eps,
                 int32_t* status, std::vector<std::vector<double>>* ci_out) {
@@ -207,6 +202,7 @@ void mbe_default_options(mbe_options* o) {
   o->keep_ci = 0;
   o->deterministic = 1;
   o->mem_cap_bytes = 0;
+  o->timing = 0;
 }
 
 int mbe_create(mbe_ctx** out, int device, const mbe_options* opt) {
@@ -228,10 +224,11 @@ int mbe_create(mbe_ctx** out, int device, const mbe_options* opt) {
   c->device = device;
   c->opt = o;
   c->pool.cap = o.mem_cap_bytes;
-  if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+  if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
     delete c;
     return MBE_ECUDA;
   }
+  c->stream = c->own_stream;
   *out = c;
   return MBE_OK;
 }
@@ -240,9 +237,17 @@ void mbe_destroy(mbe_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
-  cudaStream_t s = ctx->stream;
+  cudaStream_t s = ctx->own_stream;
   delete ctx;
   cudaStreamDestroy(s);
+}
+
+int mbe_set_stream(mbe_ctx* ctx, void* stream) {
+  return guarded(ctx, [&]() -> int {
+    CU_CHECK(cudaStreamSynchronize(ctx->stream));
+    ctx->stream = stream ? (cudaStream_t)stream : ctx->own_stream;
+    return MBE_OK;
+  });
 }
 
 const char* mbe_last_error(const mbe_ctx* ctx) {
@@ -531,14 +536,54 @@ int mbe_energy_backward(mbe_ctx* ctx, double scale, double* dh, double* deri) {
 
 int mbe_get_stats(const mbe_ctx* ctx, mbe_stats* out) {
   if (!ctx || !out) return MBE_EINVAL;
+  mbe_ctx* c = const_cast<mbe_ctx*>(ctx);
+  cudaSetDevice(c->device);
+  c->dom_timer.resolve();
   *out = ctx->stats;
+  out->launches = __atomic_load_n(&g_mbe_launches, __ATOMIC_RELAXED) - ctx->launch_base;
+  out->dom_ms = c->dom_timer.ms;
   return MBE_OK;
 }
 
 int mbe_reset_stats(mbe_ctx* ctx) {
   if (!ctx) return MBE_EINVAL;
+  cudaSetDevice(ctx->device);
+  ctx->dom_timer.resolve();
+  ctx->dom_timer.ms = 0.0;
   ctx->stats = mbe_stats{};
+  ctx->launch_base = __atomic_load_n(&g_mbe_launches, __ATOMIC_RELAXED);
   return MBE_OK;
+}
+
+int mbe_set_order_energies(mbe_ctx* ctx, int order, const int32_t* tuples, int64_t ntup,
+                           const double* eps) {
+  return guarded(ctx, [&]() -> int {
+    if (!ctx->have_ref) return fail(ctx, MBE_ESTATE, "no reference space set");
+    if (order < 1 || order > MBE_MAX_ORDER || ntup < 0 || (ntup && (!tuples || !eps)))
+      return fail(ctx, MBE_EINVAL, "bad order or tuple arguments");
+    std::set<int> expset(ctx->exp.begin(), ctx->exp.end());
+    for (int64_t t = 0; t < ntup; t++) {
+      const int32_t* row = tuples + t * order;
+      if (!std::isfinite(eps[t])) return fail(ctx, MBE_EINVAL, "non-finite energy");
+      for (int i = 0; i < order; i++) {
+        if (!expset.count(row[i])) return fail(ctx, MBE_EINVAL, "tuple orbital not in expansion space");
+        if (i && row[i] <= row[i - 1]) return fail(ctx, MBE_EINVAL, "tuple rows must be strictly ascending");
+      }
+    }
+    ctx->cur_order = order;
+    ctx->cur_tuples.assign(tuples, tuples + ntup * order);
+    ctx->cur_eps.assign(eps, eps + ntup);
+    ctx->cur_tuples_dev.reset(&ctx->pool, (size_t)ntup * order);
+    ctx->cur_eps_dev.reset(&ctx->pool, ntup);
+    if (ntup) {
+      CU_CHECK(cudaMemcpyAsync(ctx->cur_tuples_dev.ptr, tuples, sizeof(int32_t) * ntup * order,
+                               cudaMemcpyHostToDevice, ctx->stream));
+      CU_CHECK(cudaMemcpyAsync(ctx->cur_eps_dev.ptr, eps, sizeof(double) * ntup,
+                               cudaMemcpyHostToDevice, ctx->stream));
+      CU_CHECK(cudaStreamSynchronize(ctx->stream));
+    }
+    return MBE_OK;
+  });
 }
 
 int mbe_sigma(mbe_ctx* ctx, const int* act, int nact, const double* c, double* sigma,

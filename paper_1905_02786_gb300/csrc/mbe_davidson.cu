@@ -551,4 +551,5 @@ void davidson_batch(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int32_t* s
   ctx->stats.casci += B;
   ctx->stats.sigma_vectors += stats_vecs;
   ctx->stats.sigma_flops += (double)stats_vecs * 2.0 * (double)N * bp.npair * bp.npair;
+  ctx->stats.dom_flops += (double)stats_vecs * 2.0 * (double)N * bp.npair * bp.npair;
 }

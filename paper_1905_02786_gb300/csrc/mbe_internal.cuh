@@ -26,7 +26,43 @@ struct MbeError {
                                     cudaGetErrorString(e_)};                \
   } while (0)
 
-#define CU_LAUNCH_CHECK() CU_CHECK(cudaGetLastError())
+// every launch site checks the launch and counts it
+extern int64_t g_mbe_launches;
+#define CU_LAUNCH_CHECK()          \
+  do {                             \
+    __atomic_add_fetch(&g_mbe_launches, 1, __ATOMIC_RELAXED); \
+    CU_CHECK(cudaGetLastError());  \
+  } while (0)
+
+// CUDA-event timing of the dominant (sigma contraction) kernel
+struct KernelTimer {
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+  double ms = 0.0;
+  void begin(cudaStream_t s, bool on, cudaEvent_t* a) {
+    *a = nullptr;
+    if (!on) return;
+    cudaEventCreate(a);
+    cudaEventRecord(*a, s);
+  }
+  void end(cudaStream_t s, cudaEvent_t a) {
+    if (!a) return;
+    cudaEvent_t b;
+    cudaEventCreate(&b);
+    cudaEventRecord(b, s);
+    pending.emplace_back(a, b);
+  }
+  void resolve() {
+    for (auto& p : pending) {
+      float t = 0.f;
+      cudaEventSynchronize(p.second);
+      cudaEventElapsedTime(&t, p.first, p.second);
+      ms += t;
+      cudaEventDestroy(p.first);
+      cudaEventDestroy(p.second);
+    }
+    pending.clear();
+  }
+};
 
 // --------------------------------------------------------- device memory
 // A caching allocator: freed blocks are kept per size and reused; the total
@@ -103,8 +139,11 @@ struct OrderRec {
 struct mbe_ctx {
   int device = 0;
   mbe_stats stats = {};
+  int64_t launch_base = 0;
+  KernelTimer dom_timer;
   mbe_options opt;
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;      // stream all work is issued on
+  cudaStream_t own_stream = nullptr;  // the context's own stream
   std::string last_error;
   DevPool pool;
 
