@@ -169,7 +169,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--max-order", type=int, default=None)
     ap.add_argument("--max-batch", type=int, default=4096)
@@ -257,8 +257,14 @@ def main():
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     pk, pk_kind = peaks()
-    dom_ms_per = st["dom_ms"] / max(st["dom_launches"], 1)
-    dom_flops_per = st["dom_flops"] / max(st["dom_launches"], 1)
+    if prec == B.MBE_FP64:
+        dom_ms_per = st["fp64_ms"] / max(st["fp64_launches"], 1)
+        dom_flops_per = st["fp64_flops"] / max(st["fp64_launches"], 1)
+        dom_launches = st["fp64_launches"]
+    else:
+        dom_ms_per = st["dom_ms"] / max(st["dom_launches"], 1)
+        dom_flops_per = st["dom_flops"] / max(st["dom_launches"], 1)
+        dom_launches = st["dom_launches"]
     achieved_tf = dom_flops_per / (dom_ms_per * 1e-3) / 1e12 if dom_ms_per > 0 else None
     if prec == B.MBE_FP64:
         kname = "k_contract_fp64"
@@ -277,7 +283,8 @@ def main():
                 "unit": "TFLOP/s", "frac": (achieved_tf / peak_tf) if achieved_tf else None,
                 "traffic": traffic, "peak_source": peak_src,
                 "flops_per_launch": dom_flops_per, "ms_per_launch": dom_ms_per,
-                "launches": st["dom_launches"]}
+                "launches": dom_launches,
+                "kernel_ms_total": dom_ms_per * dom_launches, "step_ms_total": t_ms}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -301,8 +308,16 @@ def main():
                            "l2": "256 MiB buffer written before each step (flushed); "
                                  "Davidson working set exceeds L2",
                            "parallelism": f"tuple-sharded x{world}" if world > 1 else "1 GPU"},
-                "sigma_tflops": (st["sigma_flops"] / (st["dom_ms"] * 1e-3) / 1e12)
-                if st["dom_ms"] else None,
+                "sigma_tflops": {
+                    "tensor_core": (st["dom_flops"] / (st["dom_ms"] * 1e-3) / 1e12)
+                    if st["dom_ms"] else None,
+                    "fp64": (st["fp64_flops"] / (st["fp64_ms"] * 1e-3) / 1e12)
+                    if st["fp64_ms"] else None,
+                    "tensor_core_ms": st["dom_ms"], "fp64_ms": st["fp64_ms"],
+                    "tensor_core_vectors_per_casci": st["dom_flops"] / max(st["sigma_flops"], 1)
+                    * st["sigma_vectors"] / max(st["casci"], 1),
+                    "fp64_vectors_per_casci": st["fp64_flops"] / max(st["sigma_flops"], 1)
+                    * st["sigma_vectors"] / max(st["casci"], 1)},
                 "davidson_iters_mean": st["iters_total"] / max(st["casci"], 1),
                 "noconv": st["noconv"],
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,

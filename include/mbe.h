@@ -79,6 +79,8 @@ typedef struct mbe_options {
                            no cap (exceeding it returns MBE_ENOMEM)          */
   int timing;           /* 1: time the sigma contraction launches with CUDA
                            events (mbe_stats.dom_ms)                         */
+  int verbose;          /* 1: print per-iteration Davidson residual summaries
+                           to stderr                                         */
 } mbe_options;
 
 typedef struct mbe_ctx mbe_ctx;
@@ -93,11 +95,14 @@ typedef struct mbe_stats {
   int64_t iters_max;      /* largest iteration count of one CASCI             */
   int64_t noconv;         /* CASCIs that hit the iteration cap                */
   int64_t launches;       /* kernel launches issued by the library            */
-  int64_t dom_launches;   /* launches of the sigma contraction kernel (FP64
-                             contraction, or the fused tensor-core sigma)     */
+  int64_t dom_launches;   /* launches of the fused tensor-core sigma kernel   */
   double dom_ms;          /* their summed device time (CUDA events on the
                              context stream); 0 unless opt.timing = 1         */
-  double dom_flops;       /* their algorithmic flops, 2 N_det npair^2 each   */
+  double dom_flops;       /* their algorithmic flops, 2 N_det npair^2 per
+                             sigma vector                                     */
+  int64_t fp64_launches;  /* launches of the FP64 (kl|ij) contraction kernel  */
+  double fp64_ms;         /* their summed device time (opt.timing = 1)        */
+  double fp64_flops;      /* their algorithmic flops                          */
 } mbe_stats;
 
 /* Fill *opt with the defaults (FP64, max_batch 256, subspace 16, 200

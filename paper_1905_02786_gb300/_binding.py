@@ -39,7 +39,7 @@ class mbe_options(ctypes.Structure):
                 ("conv_tol_r", ctypes.c_double), ("conv_tol_e", ctypes.c_double),
                 ("spin_shift", ctypes.c_double), ("keep_ci", ctypes.c_int),
                 ("deterministic", ctypes.c_int), ("mem_cap_bytes", ctypes.c_int64),
-                ("timing", ctypes.c_int)]
+                ("timing", ctypes.c_int), ("verbose", ctypes.c_int)]
 
 
 _lib = None
@@ -227,7 +227,9 @@ class mbe_stats(ctypes.Structure):
                 ("sigma_flops", ctypes.c_double), ("iters_total", ctypes.c_int64),
                 ("iters_max", ctypes.c_int64), ("noconv", ctypes.c_int64),
                 ("launches", ctypes.c_int64), ("dom_launches", ctypes.c_int64),
-                ("dom_ms", ctypes.c_double), ("dom_flops", ctypes.c_double)]
+                ("dom_ms", ctypes.c_double), ("dom_flops", ctypes.c_double),
+                ("fp64_launches", ctypes.c_int64), ("fp64_ms", ctypes.c_double),
+                ("fp64_flops", ctypes.c_double)]
 
 
 def mbe_set_order_energies(ctx, tuples, eps, order: int | None = None):

@@ -195,7 +195,7 @@ void mbe_default_options(mbe_options* o) {
   o->precision = MBE_FP64;
   o->max_batch = 256;
   o->max_subspace = 20;
-  o->max_iter = 200;
+  o->max_iter = 400;
   o->conv_tol_r = 1e-8;
   o->conv_tol_e = 1e-12;
   o->spin_shift = 0.5;
@@ -203,6 +203,7 @@ void mbe_default_options(mbe_options* o) {
   o->deterministic = 1;
   o->mem_cap_bytes = 0;
   o->timing = 0;
+  o->verbose = 0;
 }
 
 int mbe_create(mbe_ctx** out, int device, const mbe_options* opt) {
@@ -539,9 +540,11 @@ int mbe_get_stats(const mbe_ctx* ctx, mbe_stats* out) {
   mbe_ctx* c = const_cast<mbe_ctx*>(ctx);
   cudaSetDevice(c->device);
   c->dom_timer.resolve();
+  c->fp64_timer.resolve();
   *out = ctx->stats;
   out->launches = __atomic_load_n(&g_mbe_launches, __ATOMIC_RELAXED) - ctx->launch_base;
   out->dom_ms = c->dom_timer.ms;
+  out->fp64_ms = c->fp64_timer.ms;
   return MBE_OK;
 }
 
@@ -550,6 +553,8 @@ int mbe_reset_stats(mbe_ctx* ctx) {
   cudaSetDevice(ctx->device);
   ctx->dom_timer.resolve();
   ctx->dom_timer.ms = 0.0;
+  ctx->fp64_timer.resolve();
+  ctx->fp64_timer.ms = 0.0;
   ctx->stats = mbe_stats{};
   ctx->launch_base = __atomic_load_n(&g_mbe_launches, __ATOMIC_RELAXED);
   return MBE_OK;
@@ -616,7 +621,14 @@ int mbe_sigma(mbe_ctx* ctx, const int* act, int nact, const double* c, double* s
     CU_CHECK(cudaMemcpyAsync(cd.ptr, c, sizeof(double) * bp.ndet, cudaMemcpyHostToDevice,
                              ctx->stream));
     SigmaWork w;
-    sigma_fp64(ctx, bp, w, cd.ptr, bp.ndet, sd.ptr, bp.ndet, nullptr, ctx->opt.spin_shift);
+    // mixed precision: the tensor-core path (valid for c = c^T, the
+    // alpha<->beta symmetric sector), else FP64
+    if (ctx->opt.precision == MBE_MIXED_BF16X3 && sigma_tc_supported(nact, bp.nstr)) {
+      sigma_tc(ctx, bp, w, cd.ptr, bp.ndet, sd.ptr, bp.ndet, nullptr, ctx->opt.spin_shift);
+      if (sigma_tc_error(ctx, w)) return fail(ctx, MBE_ECUDA, "tensor-core sigma wait timed out");
+    } else {
+      sigma_fp64(ctx, bp, w, cd.ptr, bp.ndet, sd.ptr, bp.ndet, nullptr, ctx->opt.spin_shift);
+    }
     CU_CHECK(cudaMemcpyAsync(sigma, sd.ptr, sizeof(double) * bp.ndet, cudaMemcpyDeviceToHost,
                              ctx->stream));
     double ec = 0.0;

@@ -510,12 +510,12 @@ void sigma_fp64(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const double* c, int
     CU_LAUNCH_CHECK();
     dim3 g2((unsigned)cblocks, nb);
     cudaEvent_t ev;
-    ctx->dom_timer.begin(ctx->stream, ctx->opt.timing != 0, &ev);
+    ctx->fp64_timer.begin(ctx->stream, ctx->opt.timing != 0, &ev);
     k_contract_fp64<<<g2, 256, smem_c, ctx->stream>>>(bp.gp.ptr, npair, w.D.ptr, ndet, active,
                                                       bmap.ptr + b0, w.E.ptr);
     CU_LAUNCH_CHECK();
-    ctx->dom_timer.end(ctx->stream, ev);
-    ctx->stats.dom_launches += 1;
+    ctx->fp64_timer.end(ctx->stream, ev);
+    ctx->stats.fp64_launches += 1;
     k_scatter_fp64<<<g1, 256, 0, ctx->stream>>>(bp.tab->link.ptr, bp.tab->masks.ptr, bp.nstr,
                                                 bp.n, bp.nsig, w.E.ptr, c, c_stride, spin_shift,
                                                 active, bmap.ptr + b0, out, out_stride);

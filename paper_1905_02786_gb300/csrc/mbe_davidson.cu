@@ -13,6 +13,7 @@
 #include "mbe_internal.cuh"
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 
 namespace {
 
@@ -191,7 +192,8 @@ __global__ void k_residual(const double* __restrict__ V, const double* __restric
 
 // convergence bookkeeping after the residual norms are known
 __global__ void k_converge(const double* __restrict__ partial, int nchunks, int B, int it,
-                           double tol_r, double tol_e, const double* __restrict__ theta,
+                           const double* __restrict__ tol_r, double tol_e, int rel,
+                           const double* __restrict__ theta,
                            double* __restrict__ theta_old, double* __restrict__ rnorm,
                            int32_t* __restrict__ active, int32_t* __restrict__ iters,
                            int32_t* __restrict__ nactive) {
@@ -204,8 +206,11 @@ __global__ void k_converge(const double* __restrict__ partial, int nchunks, int 
     for (int c = 0; c < nchunks; c++) s += partial[(int64_t)b * nchunks + c];
     double rn = sqrt(s);
     rnorm[b] = rn;
-    iters[b] = it + 1;
-    bool conv = it > 0 && fabs(theta[b] - theta_old[b]) < tol_e && rn < tol_r;
+    iters[b] += 1;
+    // rel: the residual tolerance scales with max(1, |theta|) (the floor of a
+    // reduced-precision sigma is relative to the size of H)
+    const double tr = rel ? tol_r[b] * fmax(1.0, fabs(theta[b])) : tol_r[b];
+    bool conv = it > 0 && fabs(theta[b] - theta_old[b]) < tol_e && rn < tr;
     theta_old[b] = theta[b];
     if (conv) active[b] = 0;
     else atomicAdd(&cnt, 1);
@@ -422,6 +427,44 @@ __global__ void k_guess(const double* __restrict__ hd, int nstr, int M, double* 
   }
 }
 
+// V[b][0] = X[b]
+__global__ void k_copy_x(const double* __restrict__ X, double* __restrict__ V, int M, int64_t N,
+                         const int32_t* __restrict__ active) {
+  const int b = blockIdx.y;
+  if (!active[b]) return;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N;
+       k += (int64_t)gridDim.x * blockDim.x)
+    V[(int64_t)b * M * N + k] = X[(int64_t)b * N + k];
+}
+
+// after an exact (FP64) sigma of x: keep refining tuples whose exact
+// residual is above target; the next mixed stage stops at a residual of
+// max(target, exact residual / 20)
+__global__ void k_refine_select(const double* __restrict__ rnorm, int B, double target,
+                                int32_t* __restrict__ active, double* __restrict__ tolr,
+                                int32_t* __restrict__ nactive) {
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    const double r = rnorm[b];
+    const int a = r > target ? 1 : 0;
+    active[b] = a;
+    tolr[b] = fmax(target, 0.05 * r);
+    if (a) atomicAdd(&cnt, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *nactive = cnt;
+}
+
+__global__ void k_fill(double* __restrict__ v, int n, double x) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = x;
+}
+
+__global__ void k_set_i32(int32_t* __restrict__ v, int n, int32_t x) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = x;
+}
+
 }  // namespace
 
 struct Multidot {
@@ -442,6 +485,15 @@ struct Multidot {
   }
 };
 
+// Davidson for one batch of tuples.
+//  FP64:  one stage with FP64 sigma vectors to conv_tol_r / conv_tol_e.
+//  mixed: stage A with tensor-core sigma vectors to a residual of 1e-3; then
+//         refinement rounds: an FP64 sigma of the current Ritz vector x gives
+//         the exact Rayleigh quotient and residual; tuples above conv_tol_r
+//         restart from {x} (with its exact A x) and continue with tensor-core
+//         sigma vectors for the correction directions, whose sigma errors
+//         scale with their small weights.  The last exact sigma provides the
+//         FP64 Rayleigh quotient that is reported.
 void davidson_batch(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int32_t* status_host,
                     double* s2_host, double* x_out_dev) {
   const int B = bp.B;
@@ -450,67 +502,44 @@ void davidson_batch(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int32_t* s
   const double shift = ctx->opt.spin_shift;
   DevPool* P = &ctx->pool;
   DevBuf<double> V(P, (size_t)B * M * N), AV(P, (size_t)B * M * N), hd(P, (size_t)B * N),
-      T(P, (size_t)B * N), Xown(P, x_out_dev ? 0 : (size_t)B * N),
-      G(P, (size_t)B * M * M), y(P, (size_t)B * M), yp(P, (size_t)B * M), theta(P, B), theta_old(P, B), rnorm(P, B), coef(P, (size_t)B * M),
+      T(P, (size_t)B * N), Xown(P, x_out_dev ? 0 : (size_t)B * N), G(P, (size_t)B * M * M),
+      y(P, (size_t)B * M), yp(P, (size_t)B * M), theta(P, B), theta_old(P, B), rnorm(P, B),
+      tolr(P, B), coef(P, (size_t)B * M), xx(P, (size_t)B * M),
       rpart(P, (size_t)B * ((N + DOT_CHUNK - 1) / DOT_CHUNK));
-  DevBuf<int32_t> active(P, B), iters(P, B), nact(P, 1), stalled(P, B);
+  DevBuf<int32_t> active(P, B), iters(P, B), nact(P, 1);
   double* X = x_out_dev ? x_out_dev : Xown.ptr;
   SigmaWork sw;
   Multidot md;
   cudaStream_t st = ctx->stream;
+  const bool mixed =
+      ctx->opt.precision == MBE_MIXED_BF16X3 && sigma_tc_supported(bp.n, bp.nstr) && N > 1;
 
   launch_hdiag(ctx, bp, shift, hd.ptr);
   k_guess<<<B, 256, 0, st>>>(hd.ptr, bp.nstr, M, V.ptr);
   CU_LAUNCH_CHECK();
-  std::vector<int32_t> ones(B, 1);
-  CU_CHECK(cudaMemcpyAsync(active.ptr, ones.data(), sizeof(int32_t) * B, cudaMemcpyHostToDevice, st));
+  k_set_i32<<<1, 256, 0, st>>>(active.ptr, B, 1);
+  CU_LAUNCH_CHECK();
   CU_CHECK(cudaMemsetAsync(iters.ptr, 0, sizeof(int32_t) * B, st));
-  CU_CHECK(cudaMemsetAsync(stalled.ptr, 0, sizeof(int32_t) * B, st));
   CU_CHECK(cudaMemsetAsync(G.ptr, 0, sizeof(double) * B * M * M, st));
+  k_fill<<<1, 256, 0, st>>>(tolr.ptr, B, mixed ? std::max(ctx->opt.conv_tol_r, 1e-3)
+                                                : ctx->opt.conv_tol_r);
+  CU_LAUNCH_CHECK();
 
   int64_t eblocks = std::min<int64_t>((N + 255) / 256, 1024);
   dim3 ge((unsigned)eblocks, B);
   const int nchunks = (int)((N + DOT_CHUNK - 1) / DOT_CHUNK);
   dim3 gc(nchunks, B);
-  int m = 1;
   const int max_iter = std::max(1, ctx->opt.max_iter);
-  int64_t stats_vecs = B;
-  for (int it = 0; it < max_iter; it++) {
-    // K4: sigma of the newest vector
-    sigma_fp64(ctx, bp, sw, V.ptr + (int64_t)(m - 1) * N, (int64_t)M * N,
-               AV.ptr + (int64_t)(m - 1) * N, (int64_t)M * N, active.ptr, shift);
-    // K5: new row of the projected matrix
-    md.run(ctx, V.ptr, (int64_t)M * N, N, AV.ptr + (int64_t)(m - 1) * N, (int64_t)M * N, m, N, B,
-           active.ptr, coef.ptr, M, 1);
-    k_store_grow<<<B, 32, 0, st>>>(coef.ptr, m, M, active.ptr, G.ptr);
-    CU_LAUNCH_CHECK();
-    // K6: Rayleigh-Ritz
-    k_jacobi<<<B, 32, 0, st>>>(G.ptr, m, M, active.ptr, theta.ptr, y.ptr);
-    CU_LAUNCH_CHECK();
-    // K7: residual and convergence
-    k_residual<<<gc, 256, 0, st>>>(V.ptr, AV.ptr, m, M, N, y.ptr, theta.ptr, active.ptr, X, T.ptr,
-                                   nchunks, rpart.ptr);
-    CU_LAUNCH_CHECK();
-    k_converge<<<1, 256, 0, st>>>(rpart.ptr, nchunks, B, it, ctx->opt.conv_tol_r,
-                                  ctx->opt.conv_tol_e, theta.ptr, theta_old.ptr, rnorm.ptr,
-                                  active.ptr, iters.ptr, nact.ptr);
-    CU_LAUNCH_CHECK();
-    int32_t nact_h = 0;
-    CU_CHECK(cudaMemcpyAsync(&nact_h, nact.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    CU_CHECK(cudaStreamSynchronize(st));
-    if (nact_h == 0) break;
-    stats_vecs += nact_h;
-    int restarted = 0;
-    if (m == M) {   // restart with {x, x_prev}
-      k_restart_coef<<<B, 32, 0, st>>>(y.ptr, yp.ptr, m, M, active.ptr, G.ptr);
-      CU_LAUNCH_CHECK();
-      k_restart_vec<<<ge, 256, 0, st>>>(V.ptr, AV.ptr, m, M, N, y.ptr, yp.ptr, active.ptr);
-      CU_LAUNCH_CHECK();
-      m = 2;
-      restarted = 1;
-    }
-    k_save_yprev<<<B, 32, 0, st>>>(y.ptr, m, M, restarted, active.ptr, yp.ptr);
-    CU_LAUNCH_CHECK();
+  int64_t vecs_tc = 0, vecs_64 = 0;
+  int total_it = 0;
+
+  auto sigma = [&](bool use_tc, const double* c, double* out) {
+    if (use_tc) sigma_tc(ctx, bp, sw, c, (int64_t)M * N, out, (int64_t)M * N, active.ptr, shift);
+    else sigma_fp64(ctx, bp, sw, c, (int64_t)M * N, out, (int64_t)M * N, active.ptr, shift);
+  };
+  // precondition the residual in T, orthogonalise it against V[0..m) and
+  // append it as V[m] (tuples whose correction vanished are frozen)
+  auto extend = [&](int m) {
     k_precondition<<<ge, 256, 0, st>>>(T.ptr, hd.ptr, bp.nstr, theta.ptr, active.ptr);
     CU_LAUNCH_CHECK();
     for (int pass = 0; pass < 2; pass++) {
@@ -523,33 +552,147 @@ void davidson_batch(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int32_t* s
     CU_LAUNCH_CHECK();
     k_fix_frozen<<<1, 256, 0, st>>>(active.ptr, B);
     CU_LAUNCH_CHECK();
-    m++;
+  };
+  auto count_active = [&]() {
+    int32_t n = 0;
+    CU_CHECK(cudaMemcpyAsync(&n, nact.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CU_CHECK(cudaStreamSynchronize(st));
+    if (ctx->opt.verbose) {
+      std::vector<double> rn(B), th(B);
+      CU_CHECK(cudaMemcpy(rn.data(), rnorm.ptr, sizeof(double) * B, cudaMemcpyDeviceToHost));
+      CU_CHECK(cudaMemcpy(th.data(), theta.ptr, sizeof(double) * B, cudaMemcpyDeviceToHost));
+      double mx = 0.0;
+      for (double r : rn) mx = std::max(mx, r);
+      fprintf(stderr, "[mbe davidson] n=%d nsig=%d B=%d it=%d active=%d max|r|=%.3e theta0=%.12f\n",
+              bp.n, bp.nsig, B, total_it, n, mx, th[0]);
+    }
+    return n;
+  };
+
+  // One stage of Davidson iterations from the current (V, AV, G): the
+  // subspace holds m_start vectors and the newest one's sigma is pending.
+  // exact0: V_0 carries an exact (FP64) A V_0; its couplings G_0j are then
+  // taken as (A V_0).V_j, which involves no reduced-precision sigma, and the
+  // stage ends before a restart would replace V_0.
+  auto stage = [&](bool use_tc, double tol_e, int rel, int m_start, int cap, int nact0,
+                   bool exact0) {
+    int m = m_start;
+    int nact_h = nact0;
+    for (int it = 0; it < cap && total_it < max_iter; it++, total_it++) {
+      sigma(use_tc, V.ptr + (int64_t)(m - 1) * N, AV.ptr + (int64_t)(m - 1) * N);
+      (use_tc ? vecs_tc : vecs_64) += nact_h;
+      md.run(ctx, V.ptr, (int64_t)M * N, N, AV.ptr + (int64_t)(m - 1) * N, (int64_t)M * N, m, N,
+             B, active.ptr, coef.ptr, M, 1);
+      if (exact0) {
+        md.run(ctx, AV.ptr, (int64_t)M * N, 0, V.ptr + (int64_t)(m - 1) * N, (int64_t)M * N, 1, N,
+               B, active.ptr, coef.ptr, M, 1);
+      }
+      k_store_grow<<<B, 32, 0, st>>>(coef.ptr, m, M, active.ptr, G.ptr);
+      CU_LAUNCH_CHECK();
+      k_jacobi<<<B, 32, 0, st>>>(G.ptr, m, M, active.ptr, theta.ptr, y.ptr);
+      CU_LAUNCH_CHECK();
+      k_residual<<<gc, 256, 0, st>>>(V.ptr, AV.ptr, m, M, N, y.ptr, theta.ptr, active.ptr, X,
+                                     T.ptr, nchunks, rpart.ptr);
+      CU_LAUNCH_CHECK();
+      k_converge<<<1, 256, 0, st>>>(rpart.ptr, nchunks, B, m_start > 1 ? it + 1 : it, tolr.ptr,
+                                    tol_e, rel, theta.ptr, theta_old.ptr, rnorm.ptr, active.ptr,
+                                    iters.ptr, nact.ptr);
+      CU_LAUNCH_CHECK();
+      nact_h = count_active();
+      if (nact_h == 0) return;
+      if (exact0 && m == M) return;   // the next exact point restarts
+      int restarted = 0;
+      if (m == M) {   // restart with {x, x_prev}
+        k_restart_coef<<<B, 32, 0, st>>>(y.ptr, yp.ptr, m, M, active.ptr, G.ptr);
+        CU_LAUNCH_CHECK();
+        k_restart_vec<<<ge, 256, 0, st>>>(V.ptr, AV.ptr, m, M, N, y.ptr, yp.ptr, active.ptr);
+        CU_LAUNCH_CHECK();
+        m = 2;
+        restarted = 1;
+      }
+      k_save_yprev<<<B, 32, 0, st>>>(y.ptr, m, M, restarted, active.ptr, yp.ptr);
+      CU_LAUNCH_CHECK();
+      extend(m);
+      m++;
+    }
+  };
+
+  // exact (FP64) sigma of the current Ritz vectors x of all tuples: V0 = x,
+  // AV0 = A x, G = [[x.Ax]], theta, the exact residual (in T) and its norm
+  auto exact_point = [&]() {
+    k_set_i32<<<1, 256, 0, st>>>(active.ptr, B, 1);
+    CU_LAUNCH_CHECK();
+    k_copy_x<<<ge, 256, 0, st>>>(X, V.ptr, M, N, active.ptr);
+    CU_LAUNCH_CHECK();
+    sigma(false, V.ptr, AV.ptr);
+    vecs_64 += B;
+    md.run(ctx, V.ptr, (int64_t)M * N, N, AV.ptr, (int64_t)M * N, 1, N, B, active.ptr, coef.ptr,
+           M, 1);
+    k_store_grow<<<B, 32, 0, st>>>(coef.ptr, 1, M, active.ptr, G.ptr);
+    CU_LAUNCH_CHECK();
+    k_jacobi<<<B, 32, 0, st>>>(G.ptr, 1, M, active.ptr, theta.ptr, y.ptr);
+    CU_LAUNCH_CHECK();
+    k_residual<<<gc, 256, 0, st>>>(V.ptr, AV.ptr, 1, M, N, y.ptr, theta.ptr, active.ptr, X,
+                                   T.ptr, nchunks, rpart.ptr);
+    CU_LAUNCH_CHECK();
+    // residual norms only (the decision is k_refine_select's)
+    k_converge<<<1, 256, 0, st>>>(rpart.ptr, nchunks, B, 0, tolr.ptr, 0.0, 0, theta.ptr,
+                                  theta_old.ptr, rnorm.ptr, active.ptr, iters.ptr, nact.ptr);
+    CU_LAUNCH_CHECK();
+    k_save_yprev<<<B, 32, 0, st>>>(y.ptr, 1, M, 1, active.ptr, yp.ptr);
+    CU_LAUNCH_CHECK();
+  };
+
+  if (!mixed) {
+    stage(false, ctx->opt.conv_tol_e, 0, 1, max_iter, B, false);
+  } else {
+    // stage A: tensor-core sigma vectors to a residual of 1e-3 max(1, |theta|)
+    // (above the split-BF16x3 floor) or at most 150 iterations
+    stage(true, 1e300, 1, 1, 150, B, false);
+    // refinement rounds: exact residual, then a bounded tensor-core stage that
+    // reduces it by 20x (or to the target)
+    const double target = std::max(ctx->opt.conv_tol_r, 3e-8);
+    for (int round = 0; round < 12; round++) {
+      exact_point();
+      k_refine_select<<<1, 256, 0, st>>>(rnorm.ptr, B, target, active.ptr, tolr.ptr, nact.ptr);
+      CU_LAUNCH_CHECK();
+      const int na = count_active();
+      if (na == 0 || total_it >= max_iter) break;
+      extend(1);   // preconditioned exact residual becomes V_1
+      stage(true, 1e300, 0, 2, 40, na, true);
+    }
+    if (sigma_tc_error(ctx, sw)) throw MbeError{MBE_ECUDA, "tensor-core sigma wait timed out"};
   }
-  // status and energies: eps = E_core + theta - shift <x|S^2|x>
-  std::vector<int32_t> act_h(B), stall_h(B), it_h(B);
+
+  // status and energies: eps = E_core + theta - shift <x|S^2|x> / <x|x>
+  std::vector<int32_t> it_h(B);
   std::vector<double> rn_h(B);
-  CU_CHECK(cudaMemcpyAsync(act_h.data(), active.ptr, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, st));
-  CU_CHECK(cudaMemcpyAsync(stall_h.data(), stalled.ptr, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, st));
   CU_CHECK(cudaMemcpyAsync(it_h.data(), iters.ptr, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, st));
   CU_CHECK(cudaMemcpyAsync(rn_h.data(), rnorm.ptr, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
   s2_apply(ctx, bp, X, N, T.ptr, N, nullptr);
   md.run(ctx, X, N, 0, T.ptr, N, 1, N, B, nullptr, coef.ptr, 1, 1);
-  std::vector<double> th(B), s2(B), ec(B);
+  md.run(ctx, X, N, 0, X, N, 1, N, B, nullptr, xx.ptr, 1, 1);
+  std::vector<double> th(B), s2(B), ec(B), nx(B);
   CU_CHECK(cudaMemcpyAsync(th.data(), theta.ptr, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
   CU_CHECK(cudaMemcpyAsync(s2.data(), coef.ptr, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+  CU_CHECK(cudaMemcpyAsync(nx.data(), xx.ptr, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
   CU_CHECK(cudaMemcpyAsync(ec.data(), bp.ecore.ptr, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
   CU_CHECK(cudaStreamSynchronize(st));
+  const double rtol = ctx->opt.conv_tol_r;
   for (int b = 0; b < B; b++) {
-    if (e_out_host) e_out_host[b] = ec[b] + th[b] - shift * s2[b];
-    if (s2_host) s2_host[b] = s2[b];
-    bool ok = !act_h[b] && (!stall_h[b] || rn_h[b] <= 100.0 * ctx->opt.conv_tol_r);
+    const double s2n = nx[b] > 0.0 ? s2[b] / nx[b] : 0.0;
+    if (e_out_host) e_out_host[b] = ec[b] + th[b] - shift * s2n;
+    if (s2_host) s2_host[b] = s2n;
+    bool ok = rn_h[b] <= (mixed ? std::max(rtol, 3e-8) : rtol) * 10.0 || N == 1;
     if (status_host) status_host[b] = ok ? MBE_OK : MBE_ENOCONV;
     ctx->stats.iters_total += it_h[b];
     ctx->stats.iters_max = std::max<int64_t>(ctx->stats.iters_max, it_h[b]);
     ctx->stats.noconv += ok ? 0 : 1;
   }
+  const double per = 2.0 * (double)N * bp.npair * bp.npair;
   ctx->stats.casci += B;
-  ctx->stats.sigma_vectors += stats_vecs;
-  ctx->stats.sigma_flops += (double)stats_vecs * 2.0 * (double)N * bp.npair * bp.npair;
-  ctx->stats.dom_flops += (double)stats_vecs * 2.0 * (double)N * bp.npair * bp.npair;
+  ctx->stats.sigma_vectors += vecs_tc + vecs_64;
+  ctx->stats.sigma_flops += (double)(vecs_tc + vecs_64) * per;
+  ctx->stats.dom_flops += (double)vecs_tc * per;      // tensor-core sigma vectors
+  ctx->stats.fp64_flops += (double)vecs_64 * per;     // FP64 sigma vectors
 }

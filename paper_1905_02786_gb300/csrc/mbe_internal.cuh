@@ -140,7 +140,8 @@ struct mbe_ctx {
   int device = 0;
   mbe_stats stats = {};
   int64_t launch_base = 0;
-  KernelTimer dom_timer;
+  KernelTimer dom_timer;     // tensor-core sigma launches
+  KernelTimer fp64_timer;    // FP64 contraction launches
   mbe_options opt;
   cudaStream_t stream = nullptr;      // stream all work is issued on
   cudaStream_t own_stream = nullptr;  // the context's own stream
@@ -204,9 +205,14 @@ void launch_hdiag(mbe_ctx* ctx, BinProblem& bp, double spin_shift, double* hd);
 // strides (elements between consecutive tuples' vectors); active may be NULL.
 struct SigmaWork {
   DevBuf<double> D, E;           // scratch for the FP64 path
-  DevBuf<float> Df;              // scratch for the mixed path
+  DevBuf<float> Xf;              // X rows of the tensor-core path (sigma = X + X^T)
+  DevBuf<int32_t> err;           // timeout flag of the tensor-core path
   int64_t sub_batch = 0;
 };
+bool sigma_tc_supported(int n, int nstr);
+void sigma_tc(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const double* c, int64_t c_stride,
+              double* out, int64_t out_stride, const int32_t* active, double spin_shift);
+int32_t sigma_tc_error(mbe_ctx* ctx, SigmaWork& w);
 void sigma_fp64(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const double* c,
                 int64_t c_stride, double* out, int64_t out_stride,
                 const int32_t* active, double spin_shift);

@@ -1,0 +1,416 @@
+// Fused mixed-precision sigma vector on the 5th-generation tensor cores
+// (tcgen05, sm_103a): string-pair gather of D into shared memory, the
+// (kl|ij) contraction E = g' D as split-BF16x3 MMAs with an FP32 accumulator
+// in tensor memory, and the scatter of E into the sigma rows, in one kernel.
+//
+// With c symmetric (the alpha<->beta symmetric Davidson vectors), D and E
+// are symmetric in the two string indices, so the alpha half of the scatter
+// is the transpose of the beta half: sigma = X + X^T with
+//   X(a, b) = 1/2 sum_P sum_k <b|E+_P|k> E_P(a, k)        (beta strings)
+// Each CTA owns R full rows a of X (kept in shared memory, no global
+// atomics) and walks the column strings k in tiles; for a tile of
+// N = 128 determinants (a, k) it
+//   1. gathers D_P(a,k) = s_a c(J_a,k) + s_k c(a,J_k) for all pairs P
+//      (rows J_a of c read coalesced from global memory, row a of c staged in
+//      shared memory) and splits it into bf16 hi + lo (K-major core-matrix
+//      layout, 16-byte vector stores),
+//   2. one elected thread issues g'_hi D_hi + g'_hi D_lo + g'_lo D_hi as
+//      tcgen05.mma (M = 128 pair rows, N = 128, K = 16 per instruction)
+//      into a 128 x 128 FP32 accumulator in TMEM and commits to an mbarrier,
+//   3. the 8 warps read E back with tcgen05.ld (warp w: TMEM lanes
+//      32 (w mod 4) .. + 31 = pairs P, columns 64 (w / 4) .. + 63) and push
+//      1/2 s E_P(a,k) into X(a, J) for the string J linked to k by P
+//      (shared-memory atomics).
+// Precision: both operands carry ~16 significant bits after the hi/lo split,
+// the dropped lo*lo term and the FP32 accumulation give sigma to ~1e-5
+// relative; the Davidson iteration corrects this with FP64 sigma vectors.
+#include "mbe_internal.cuh"
+#include <cuda_bf16.h>
+#include <algorithm>
+
+namespace {
+
+constexpr int TC_THREADS = 256;
+constexpr int TC_N = 128;        // determinants per MMA tile (R rows x W cols)
+constexpr int TC_M = 128;        // pair rows of the accumulator (npair <= 120 padded)
+constexpr uint32_t TMEM_COLS = 128;
+constexpr long long SPIN_LIMIT = 1LL << 28;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// K-major, no-swizzle canonical layout: core matrices of 8 rows x 16 bytes
+// (8 bf16 along K), row r of a core at +16 r; the next core along K at
+// +LBO = 128 bytes, the next group of 8 rows at +SBO = (Kpad/8) * 128 bytes.
+__device__ __forceinline__ uint32_t kmajor_offset(int row, int k, int kpad) {
+  return (uint32_t)(((row >> 3) * (kpad >> 3) + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+// shared-memory matrix descriptor (tcgen05): start address, LBO, SBO in
+// 16-byte units, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;   // version
+  return d;                 // base offset 0, layout type 0 (no swizzle)
+}
+
+// instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(mbar))
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* mbar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count));
+}
+
+// bounded wait on an mbarrier phase; returns false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t phase) {
+  uint32_t addr = smem_u32(mbar);
+  for (long long i = 0; i < SPIN_LIMIT; i++) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(phase)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
+struct TcShared {
+  // byte offsets into dynamic shared memory
+  uint32_t a_hi, a_lo, b_hi, b_lo, c_rows, x_rows, link_k, link_a, total;
+};
+
+__host__ __device__ inline TcShared tc_layout(int kpad, int R, int nstr, int npair, int W) {
+  TcShared s;
+  uint32_t o = 0;
+  auto take = [&](uint32_t bytes) {
+    uint32_t r = o;
+    o += (bytes + 127u) & ~127u;
+    return r;
+  };
+  s.a_hi = take((uint32_t)TC_M * kpad * 2);
+  s.a_lo = take((uint32_t)TC_M * kpad * 2);
+  s.b_hi = take((uint32_t)TC_N * kpad * 2);
+  s.b_lo = take((uint32_t)TC_N * kpad * 2);
+  s.c_rows = take((uint32_t)R * nstr * 4);
+  s.x_rows = take((uint32_t)R * nstr * 4);
+  s.link_k = take((uint32_t)npair * (W + 1) * 4);
+  s.link_a = take((uint32_t)R * npair * 4);
+  s.total = o;
+  return s;
+}
+
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(x);
+  lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// One CTA = tuple b (blockIdx.y) x rows [a0, a0 + R) (blockIdx.x).
+__global__ void __launch_bounds__(TC_THREADS, 1)
+k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad, int R,
+           const double* __restrict__ gp_all, const double* __restrict__ c, int64_t c_stride,
+           const int32_t* __restrict__ active, float* __restrict__ X, int64_t x_stride,
+           int32_t* __restrict__ err) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const int W = TC_N / R;
+  const int a0 = blockIdx.x * R;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tmem_base_sh;
+  const TcShared L = tc_layout(kpad, R, nstr, npair, W);
+  uint8_t* sA_hi = smem + L.a_hi;
+  uint8_t* sA_lo = smem + L.a_lo;
+  uint8_t* sB_hi = smem + L.b_hi;
+  uint8_t* sB_lo = smem + L.b_lo;
+  float* sC = (float*)(smem + L.c_rows);
+  float* sX = (float*)(smem + L.x_rows);
+  int32_t* sLk = (int32_t*)(smem + L.link_k);     // [P][W + 1]
+  int32_t* sLa = (int32_t*)(smem + L.link_a);     // [r][P]
+  const double* cb = c + (int64_t)b * c_stride;
+  const int64_t N = (int64_t)nstr * nstr;
+
+  // ---- setup: g' split into bf16 hi/lo (rows >= npair and K >= npair zero)
+  const double* g = gp_all + (int64_t)b * npair * npair;
+  for (int it = tid; it < TC_M * (kpad >> 3); it += TC_THREADS) {
+    const int row = it / (kpad >> 3), kb = (it % (kpad >> 3)) * 8;
+    __align__(16) __nv_bfloat16 h8[8], l8[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+      const int k = kb + j;
+      // split the FP64 value: hi from the double, lo from the remainder
+      const double dv = (row < npair && k < npair) ? g[(int64_t)row * npair + k] : 0.0;
+      const __nv_bfloat16 hh = __double2bfloat16(dv);
+      h8[j] = hh;
+      l8[j] = __double2bfloat16(dv - (double)__bfloat162float(hh));
+    }
+    const uint32_t off = kmajor_offset(row, kb, kpad);
+    *(uint4*)(sA_hi + off) = *(uint4*)h8;
+    *(uint4*)(sA_lo + off) = *(uint4*)l8;
+  }
+  for (int it = tid; it < R * nstr; it += TC_THREADS) {
+    const int r = it / nstr, k = it % nstr;
+    const int a = a0 + r;
+    sC[it] = a < nstr ? (float)cb[(int64_t)a * nstr + k] : 0.f;
+    sX[it] = 0.f;
+  }
+  for (int it = tid; it < R * npair; it += TC_THREADS) {
+    const int r = it / npair, P = it % npair;
+    const int a = a0 + r;
+    sLa[it] = a < nstr ? link[(int64_t)a * npair + P] : -1;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base_sh)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    mbar_init(&mbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base_sh;
+  const uint32_t idesc = make_idesc(TC_M, TC_N);
+  const uint32_t sbo = (uint32_t)(kpad >> 3) * 128u;
+  uint32_t phase = 0;
+  bool ok = true;
+
+  for (int k0 = 0; k0 < nstr && ok; k0 += W) {
+    // ---- link entries of the column strings of this tile, [P][j]
+    for (int it = tid; it < W * npair; it += TC_THREADS) {
+      const int j = it / npair, P = it % npair;
+      const int k = k0 + j;
+      sLk[P * (W + 1) + j] = k < nstr ? link[(int64_t)k * npair + P] : -1;
+    }
+    __syncthreads();
+    // ---- gather D (column n = r * W + j <-> determinant (a0 + r, k0 + j))
+    for (int it = tid; it < TC_N * (kpad >> 3); it += TC_THREADS) {
+      const int n = it % TC_N, pb = (it / TC_N) * 8;
+      const int r = n / W, j = n % W;
+      const int a = a0 + r, k = k0 + j;
+      __align__(16) __nv_bfloat16 h8[8], l8[8];
+#pragma unroll
+      for (int q = 0; q < 8; q++) {
+        const int P = pb + q;
+        float v = 0.f;
+        if (P < npair && a < nstr && k < nstr) {
+          const int32_t ta = sLa[r * npair + P];
+          if (ta >= 0) {
+            float x = (float)cb[(int64_t)(ta >> 1) * nstr + k];
+            v += (ta & 1) ? -x : x;
+          }
+          const int32_t tk = sLk[P * (W + 1) + j];
+          if (tk >= 0) {
+            float x = sC[r * nstr + (tk >> 1)];
+            v += (tk & 1) ? -x : x;
+          }
+        }
+        split_bf16(v, h8[q], l8[q]);
+      }
+      const uint32_t off = kmajor_offset(n, pb, kpad);
+      *(uint4*)(sB_hi + off) = *(uint4*)h8;
+      *(uint4*)(sB_lo + off) = *(uint4*)l8;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // ---- MMA: E = g'_hi D_hi + g'_hi D_lo + g'_lo D_hi
+    if (tid == 0) {
+      const uint32_t ahi = smem_u32(sA_hi), alo = smem_u32(sA_lo);
+      const uint32_t bhi = smem_u32(sB_hi), blo = smem_u32(sB_lo);
+      uint32_t acc = 0;
+      for (int ks = 0; ks < (kpad >> 4); ks++) {
+        const uint32_t koff = (uint32_t)ks * 256u;   // two core matrices along K
+        mma_bf16(tmem, make_desc(ahi + koff, 128, sbo), make_desc(bhi + koff, 128, sbo), idesc, acc);
+        acc = 1;
+        mma_bf16(tmem, make_desc(ahi + koff, 128, sbo), make_desc(blo + koff, 128, sbo), idesc, 1);
+        mma_bf16(tmem, make_desc(alo + koff, 128, sbo), make_desc(bhi + koff, 128, sbo), idesc, 1);
+      }
+      mma_commit(&mbar);
+    }
+    const int timed_out = mbar_wait(&mbar, phase) ? 0 : 1;
+    if (__syncthreads_or(timed_out)) {   // block-uniform decision
+      ok = false;
+      if (tid == 0) atomicExch(err, MBE_ECUDA);
+    }
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // ---- epilogue: E from TMEM, push 1/2 s E into X rows
+    if (ok) {
+      const int P = 32 * (warp & 3) + lane;
+      const int col0 = 64 * (warp >> 2);
+      for (int cc = 0; cc < 64; cc += 16) {
+        float e[16];
+        tmem_ld16(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(col0 + cc), e);
+        if (P < npair) {
+#pragma unroll
+          for (int q = 0; q < 16; q++) {
+            const int n = col0 + cc + q;
+            const int r = n / W, j = n % W;
+            if (a0 + r >= nstr || k0 + j >= nstr) continue;
+            const int32_t t = sLk[P * (W + 1) + j];
+            if (t >= 0) atomicAdd(&sX[r * nstr + (t >> 1)], (t & 1) ? -0.5f * e[q] : 0.5f * e[q]);
+          }
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+  // ---- write the X rows
+  for (int it = tid; it < R * nstr; it += TC_THREADS) {
+    const int r = it / nstr, k = it % nstr;
+    const int a = a0 + r;
+    if (a < nstr) X[(int64_t)b * x_stride + (int64_t)a * nstr + k] = sX[it];
+  }
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+  (void)N;
+}
+
+// sigma(a,b) = X(a,b) + X(b,a) + shift (S^2 c)(a,b), FP64 output
+__global__ void k_sigma_tc_finish(const float* __restrict__ X, int64_t x_stride,
+                                  const int32_t* __restrict__ link, const uint32_t* __restrict__ masks,
+                                  int nstr, int n, int nsig, const double* __restrict__ c,
+                                  int64_t c_stride, double shift, const int32_t* __restrict__ active,
+                                  double* __restrict__ out, int64_t out_stride) {
+  const int b = blockIdx.z;
+  if (active && !active[b]) return;
+  // 32 x 32 tile with its transpose staged in shared memory
+  __shared__ float tT[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  const float* Xb = X + (int64_t)b * x_stride;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int row = bx + i, col = by + threadIdx.x;     // element (bx+i, by+tx) of X
+    tT[threadIdx.x][i] = (row < nstr && col < nstr) ? Xb[(int64_t)row * nstr + col] : 0.f;
+  }
+  __syncthreads();
+  const int npair = n * (n + 1) / 2;
+  const double* cb = c + (int64_t)b * c_stride;
+  double* ob = out + (int64_t)b * out_stride;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int ia = by + i, ib = bx + threadIdx.x;       // output (ia, ib): X(ia,ib) + X(ib,ia)
+    if (ia >= nstr || ib >= nstr) continue;
+    const int64_t idx = (int64_t)ia * nstr + ib;
+    double v = (double)Xb[idx] + (double)tT[i][threadIdx.x];
+    if (shift != 0.0) {
+      const int32_t* la = link + (int64_t)ia * npair;
+      const int32_t* lb = link + (int64_t)ib * npair;
+      uint32_t ma = masks[ia], mb = masks[ib];
+      double s2 = (double)(nsig - __popc(ma & mb)) * cb[idx];
+      uint32_t oa = ma & ~mb, obm = mb & ~ma;
+      for (int q = 0; q < n; q++) {
+        if (!((oa >> q) & 1)) continue;
+        for (int p = 0; p < n; p++) {
+          if (!((obm >> p) & 1)) continue;
+          int P = p > q ? p * (p + 1) / 2 + q : q * (q + 1) / 2 + p;
+          int32_t ta = la[P], tb = lb[P];
+          double x = cb[(int64_t)(ta >> 1) * nstr + (tb >> 1)];
+          s2 -= ((ta ^ tb) & 1) ? -x : x;
+        }
+      }
+      v += shift * s2;
+    }
+    ob[idx] = v;
+  }
+}
+
+}  // namespace
+
+bool sigma_tc_supported(int n, int nstr) {
+  const int npair = n * (n + 1) / 2;
+  if (npair > TC_M) return false;
+  const int kpad = ((npair + 15) / 16) * 16;
+  const int R = nstr <= 2048 ? 2 : 1;
+  TcShared L = tc_layout(kpad, R, nstr, npair, TC_N / R);
+  return L.total + 2048 <= 227 * 1024;
+}
+
+void sigma_tc(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const double* c, int64_t c_stride,
+              double* out, int64_t out_stride, const int32_t* active, double spin_shift) {
+  const int npair = bp.npair, nstr = bp.nstr;
+  const int kpad = ((npair + 15) / 16) * 16;
+  const int R = nstr <= 2048 ? 2 : 1;
+  const TcShared L = tc_layout(kpad, R, nstr, npair, TC_N / R);
+  if (L.total + 2048 > 227 * 1024 || npair > TC_M)
+    throw MbeError{MBE_EINVAL, "active space too large for the tensor-core sigma"};
+  const int64_t N = bp.ndet;
+  if (w.Xf.n < (size_t)bp.B * N) w.Xf.reset(&ctx->pool, (size_t)bp.B * N);
+  if (!w.err.ptr) w.err.reset(&ctx->pool, 1);
+  static int attr_done[64] = {0};
+  if (!attr_done[ctx->device]) {
+    CU_CHECK(cudaFuncSetAttribute(k_sigma_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  227 * 1024 - 1024));
+    attr_done[ctx->device] = 1;
+  }
+  CU_CHECK(cudaMemsetAsync(w.err.ptr, 0, sizeof(int32_t), ctx->stream));
+  dim3 grid((unsigned)((nstr + R - 1) / R), bp.B);
+  cudaEvent_t ev;
+  ctx->dom_timer.begin(ctx->stream, ctx->opt.timing != 0, &ev);
+  k_sigma_tc<<<grid, TC_THREADS, L.total, ctx->stream>>>(bp.tab->link.ptr, nstr, npair, kpad, R,
+                                                          bp.gp.ptr, c, c_stride, active, w.Xf.ptr,
+                                                          N, w.err.ptr);
+  CU_LAUNCH_CHECK();
+  ctx->dom_timer.end(ctx->stream, ev);
+  ctx->stats.dom_launches += 1;
+  dim3 g2((unsigned)((nstr + 31) / 32), (unsigned)((nstr + 31) / 32), bp.B);
+  k_sigma_tc_finish<<<g2, dim3(32, 8), 0, ctx->stream>>>(w.Xf.ptr, N, bp.tab->link.ptr,
+                                                         bp.tab->masks.ptr, nstr, bp.n, bp.nsig, c,
+                                                         c_stride, spin_shift, active, out,
+                                                         out_stride);
+  CU_LAUNCH_CHECK();
+}
+
+int32_t sigma_tc_error(mbe_ctx* ctx, SigmaWork& w) {
+  if (!w.err.ptr) return 0;
+  int32_t e = 0;
+  CU_CHECK(cudaMemcpyAsync(&e, w.err.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  CU_CHECK(cudaStreamSynchronize(ctx->stream));
+  return e;
+}

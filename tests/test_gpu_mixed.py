@@ -1,0 +1,92 @@
+"""GPU parity of the mixed-precision path (tcgen05 split-BF16x3 sigma with
+FP64 refinement) against the oracle.
+
+Tolerances: sigma vectors element by element to 2e-4 of the largest element
+(split-BF16x3 carries ~16 significant bits per operand); CASCI energies and
+increments to 1e-7 Eh (the mixed-precision target), checked tighter (1e-8)
+for the per-tuple energies because increments combine up to 2^n of them.
+"""
+import numpy as np
+import pytest
+
+import mbe_synth as ms
+from oracle import casci as oc
+from oracle import mbe as om
+
+from test_gpu_parity import core_signs
+
+pytestmark = pytest.mark.gpu
+TOL_MIXED_INC = 1e-7
+TOL_MIXED_EPS = 1e-8
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1905_02786_gb300 import build, _binding
+    build.build()
+    _binding.load_library()
+    return _binding
+
+
+def mixed(lib, **opts):
+    return lib.MBE(0, precision=lib.MBE_MIXED_BF16X3, **opts)
+
+
+@pytest.mark.parametrize("case", [
+    (8, 3, 1, [0, 1, 2, 3, 4, 5]),                  # npair 21, one column tile
+    (12, 4, 0, [0, 1, 2, 3, 4, 5, 6, 7, 8]),        # 126 strings, ragged tiles
+    (14, 4, 2, list(range(12))),                    # 8e/12o: 495 strings, npair 78
+    (16, 1, 3, list(range(14))),                    # 2e/14o: npair 105 (Kpad 112)
+    (10, 4, 5, [1, 3, 4, 5, 7, 8, 9]),              # inactive core + deleted virtuals
+])
+@pytest.mark.parametrize("shift", [0.0, 0.5])
+def test_sigma_tc_elementwise(lib, case, shift):
+    norb, nocc, seed, act = case
+    h, eri, _ = ms.gen_integrals(norb, nocc, seed)
+    sp = oc.Space(h, eri, nocc, act)
+    m = mixed(lib, spin_shift=shift)
+    m.load(h, eri, 2 * nocc)
+    c = ms.random_symmetric_ci(sp.nstr, seed)[0]
+    sig, ecore = lib.mbe_sigma(m.ctx, act, c)
+    S = core_signs(sp, nocc, act)
+    cs = S * c.ravel()
+    ref = S * (sp.sigma(cs) + shift * sp.s2(cs) - ecore * cs)
+    scale = np.abs(ref).max()
+    err = np.abs(sig - ref).max()
+    assert err <= 2e-4 * scale, (err, scale)
+    # and exactly symmetric (sigma = X + X^T)
+    s2 = sig.reshape(sp.nstr, sp.nstr)
+    assert np.array_equal(s2, s2.T) or shift != 0.0
+    m.close()
+
+
+def test_mixed_casci_energies_vs_oracle(lib):
+    w = ms.workload("h2o_dz_8e23o")
+    h, eri, _ = ms.workload_integrals("h2o_dz_8e23o")
+    m = mixed(lib)
+    m.load(h, eri, w["nel"])
+    e_ref = lib.mbe_set_reference(m.ctx, w["ref"], w["exp"])
+    assert abs(e_ref - oc.casci(h, eri, w["nocc"], w["ref"])) < TOL_MIXED_EPS
+    for k, tk in ((1, [(0,), (7,), (22,)]), (2, [(0, 7), (8, 9)]), (3, [(0, 7, 8), (9, 10, 11)])):
+        eps, st = lib.mbe_solve_tuples(m.ctx, np.array(tk), k)
+        assert np.all(st == 0)
+        for t, e in zip(tk, eps):
+            e_or = oc.casci(h, eri, w["nocc"], om.active_space(w["ref"], t))
+            assert abs(e - e_or) < TOL_MIXED_EPS, (t, e, e_or)
+    m.close()
+
+
+def test_mixed_screened_expansion_vs_oracle(lib):
+    n, nocc = 10, 3
+    h, eri, _ = ms.gen_integrals(n, nocc, 31)
+    ref, exp = [2, 3], [0, 1, 4, 5, 6, 7, 8, 9]
+    thr = 1e-4
+    ores = om.run_mbe(h, eri, nocc, ref, exp, 4, thr)
+    m = mixed(lib)
+    m.load(h, eri, 2 * nocc)
+    res = m.run(ref, exp, 4, thr)
+    for g, o in zip(res["orders"], ores["orders"]):
+        assert [tuple(int(x) for x in t) for t in g["tuples"]] == o["tuples"]
+        assert np.abs(g["inc"] - np.array(o["inc"])).max() < TOL_MIXED_INC
+    assert abs(res["total"] - ores["total"]) < TOL_MIXED_INC
+    m.close()
