@@ -57,11 +57,17 @@ enum {
 
 /* Precision of the sigma-vector contraction. */
 enum {
-  MBE_FP64 = 0,        /* every step in FP64                                 */
-  MBE_MIXED_BF16X3 = 1 /* sigma contraction as split-BF16x3 on tcgen05 tensor
-                          cores with FP32 accumulation; Rayleigh-Ritz,
-                          orthogonalisation, final Rayleigh quotient and sums
-                          in FP64                                            */
+  MBE_FP64 = 0,          /* every step in FP64 (CUDA-core FP64 contraction)  */
+  MBE_MIXED_BF16X3 = 1,  /* Davidson sigma vectors as split-BF16x3 on tcgen05
+                            tensor cores with FP32 accumulation (fused
+                            gather/contraction/scatter); refinement rounds and
+                            the final Rayleigh quotient with FP64-grade sigma
+                            vectors (MBE_EMULATED_FP64 contraction); Ritz
+                            step, orthogonalisation and sums in FP64          */
+  MBE_EMULATED_FP64 = 2  /* every sigma vector with the (kl|ij) contraction
+                            emulated to ~1e-10 relative on tcgen05 tensor
+                            cores (exact 8-bit slices, grouped FP32
+                            accumulators, FP64 recombination)                */
 };
 
 typedef struct mbe_options {

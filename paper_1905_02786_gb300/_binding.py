@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libmbe.so")
 
 MBE_OK, MBE_EINVAL, MBE_ENOMEM, MBE_ECUDA, MBE_ENOCONV, MBE_ELOOKUP, MBE_ESTATE = \
     0, -1, -2, -3, -4, -5, -6
-MBE_FP64, MBE_MIXED_BF16X3 = 0, 1
+MBE_FP64, MBE_MIXED_BF16X3, MBE_EMULATED_FP64 = 0, 1, 2
 ERROR_NAMES = {0: "MBE_OK", -1: "MBE_EINVAL", -2: "MBE_ENOMEM", -3: "MBE_ECUDA",
                -4: "MBE_ENOCONV", -5: "MBE_ELOOKUP", -6: "MBE_ESTATE"}
 

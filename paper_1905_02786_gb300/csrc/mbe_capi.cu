@@ -160,7 +160,12 @@ void solve_jobs(mbe_ctx* ctx, const std::vector<std::vector<int>>& acts, double*
       if (ci_out) X.reset(&ctx->pool, (size_t)B * N);
       std::vector<double> e(B);
       std::vector<int32_t> s(B);
-      davidson_batch(ctx, bp, e.data(), s.data(), nullptr, ci_out ? X.ptr : nullptr);
+      const bool mixed = ctx->opt.precision == MBE_MIXED_BF16X3 && N > 1 &&
+                         sigma_tc_supported(n, tab->nstr) && ozaki_supported(tab->npair);
+      if (mixed)
+        davidson_batch_mixed(ctx, bp, e.data(), s.data(), ci_out ? X.ptr : nullptr);
+      else
+        davidson_batch(ctx, bp, e.data(), s.data(), nullptr, ci_out ? X.ptr : nullptr);
       for (int b = 0; b < B; b++) {
         if (eps) eps[idx[c0 + b]] = e[b];
         if (status) status[idx[c0 + b]] = s[b];
@@ -212,7 +217,9 @@ int mbe_create(mbe_ctx** out, int device, const mbe_options* opt) {
   mbe_options o;
   mbe_default_options(&o);
   if (opt) o = *opt;
-  if (o.precision != MBE_FP64 && o.precision != MBE_MIXED_BF16X3) return MBE_EINVAL;
+  if (o.precision != MBE_FP64 && o.precision != MBE_MIXED_BF16X3 &&
+      o.precision != MBE_EMULATED_FP64)
+    return MBE_EINVAL;
   if (o.max_batch < 1 || o.max_subspace < 4 || o.max_subspace > 32 || o.max_iter < 1)
     return MBE_EINVAL;
   int ndev = 0;
@@ -624,10 +631,26 @@ int mbe_sigma(mbe_ctx* ctx, const int* act, int nact, const double* c, double* s
     // mixed precision: the tensor-core path (valid for c = c^T, the
     // alpha<->beta symmetric sector), else FP64
     if (ctx->opt.precision == MBE_MIXED_BF16X3 && sigma_tc_supported(nact, bp.nstr)) {
-      sigma_tc(ctx, bp, w, cd.ptr, bp.ndet, sd.ptr, bp.ndet, nullptr, ctx->opt.spin_shift);
+      // the mixed mode keeps its vectors in FP32
+      std::vector<float> cf(c, c + bp.ndet), sf(bp.ndet);
+      DevBuf<float> cdf(&ctx->pool, bp.ndet), sdf(&ctx->pool, bp.ndet);
+      CU_CHECK(cudaMemcpyAsync(cdf.ptr, cf.data(), sizeof(float) * bp.ndet, cudaMemcpyHostToDevice,
+                               ctx->stream));
+      sigma_tc(ctx, bp, w, cdf.ptr, bp.ndet, sdf.ptr, bp.ndet, nullptr, ctx->opt.spin_shift);
       if (sigma_tc_error(ctx, w)) return fail(ctx, MBE_ECUDA, "tensor-core sigma wait timed out");
+      CU_CHECK(cudaMemcpyAsync(sf.data(), sdf.ptr, sizeof(float) * bp.ndet, cudaMemcpyDeviceToHost,
+                               ctx->stream));
+      double ec = 0.0;
+      CU_CHECK(cudaMemcpyAsync(&ec, bp.ecore.ptr, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+      CU_CHECK(cudaStreamSynchronize(ctx->stream));
+      for (int64_t i = 0; i < bp.ndet; i++) sigma[i] = sf[i];
+      if (e_core) *e_core = ec;
+      return MBE_OK;
     } else {
-      sigma_fp64(ctx, bp, w, cd.ptr, bp.ndet, sd.ptr, bp.ndet, nullptr, ctx->opt.spin_shift);
+      const bool emu = ctx->opt.precision == MBE_EMULATED_FP64 && ozaki_supported(bp.npair);
+      sigma_fp64(ctx, bp, w, cd.ptr, bp.ndet, sd.ptr, bp.ndet, nullptr, ctx->opt.spin_shift, emu);
+      if (emu && sigma_tc_error(ctx, w))
+        return fail(ctx, MBE_ECUDA, "tensor-core contraction wait timed out");
     }
     CU_CHECK(cudaMemcpyAsync(sigma, sd.ptr, sizeof(double) * bp.ndet, cudaMemcpyDeviceToHost,
                              ctx->stream));

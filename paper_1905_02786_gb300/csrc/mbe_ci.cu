@@ -387,8 +387,16 @@ __global__ void __launch_bounds__(256) k_contract_fp64(const double* __restrict_
 // sigma(Ia,Ib) = 1/2 sum_P [s_a E_P(Ja,Ib) + s_b E_P(Ia,Jb)] + shift (S^2 c)(Ia,Ib)
 // S^2 c = (nsig - ndocc) c - sum over pairs {p,q} with Ia holding one of them
 // and Ib the other of s_a s_b c(Ja, Jb)   (S^2 = N_beta - sum E^a_qp E^b_pq)
+// E element i: FP64, or (pair_e) the float pair hi + lo written by the
+// sliced tensor-core contraction
+__device__ __forceinline__ double load_e(const double* __restrict__ Eb, int64_t i, int pair_e) {
+  if (!pair_e) return Eb[i];
+  const float2 v = reinterpret_cast<const float2*>(Eb)[i];
+  return (double)v.x + (double)v.y;
+}
+
 __global__ void k_scatter_fp64(const int32_t* __restrict__ link, const uint32_t* __restrict__ masks,
-                               int nstr, int n, int nsig, const double* __restrict__ E,
+                               int nstr, int n, int nsig, const double* __restrict__ E, int pair_e,
                                const double* __restrict__ c, int64_t c_stride, double shift,
                                const int32_t* __restrict__ active, const int32_t* __restrict__ bmap,
                                double* __restrict__ out, int64_t out_stride) {
@@ -409,11 +417,11 @@ __global__ void k_scatter_fp64(const int32_t* __restrict__ link, const uint32_t*
     for (int P = 0; P < npair; P++) {
       int32_t ta = la[P], tb = lb[P];
       if (ta >= 0) {
-        double x = Eb[(int64_t)P * ndet + (int64_t)(ta >> 1) * nstr + ib];
+        double x = load_e(Eb, (int64_t)P * ndet + (int64_t)(ta >> 1) * nstr + ib, pair_e);
         acc += (ta & 1) ? -x : x;
       }
       if (tb >= 0) {
-        double x = Eb[(int64_t)P * ndet + (int64_t)ia * nstr + (tb >> 1)];
+        double x = load_e(Eb, (int64_t)P * ndet + (int64_t)ia * nstr + (tb >> 1), pair_e);
         acc += (tb & 1) ? -x : x;
       }
     }
@@ -473,8 +481,13 @@ __global__ void k_s2(const int32_t* __restrict__ link, const uint32_t* __restric
 }  // namespace
 
 void sigma_fp64(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const double* c, int64_t c_stride,
-                double* out, int64_t out_stride, const int32_t* active, double spin_shift) {
+                double* out, int64_t out_stride, const int32_t* active, double spin_shift,
+                bool emulated) {
   const int npair = bp.npair;
+  if (emulated && !w.err.ptr) {
+    w.err.reset(&ctx->pool, 1);
+    CU_CHECK(cudaMemsetAsync(w.err.ptr, 0, sizeof(int32_t), ctx->stream));
+  }
   const int64_t ndet = bp.ndet;
   // sub-batch so that D and E stay within ~2 GB each
   int64_t per = (int64_t)npair * ndet;
@@ -511,13 +524,18 @@ void sigma_fp64(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const double* c, int
     dim3 g2((unsigned)cblocks, nb);
     cudaEvent_t ev;
     ctx->fp64_timer.begin(ctx->stream, ctx->opt.timing != 0, &ev);
-    k_contract_fp64<<<g2, 256, smem_c, ctx->stream>>>(bp.gp.ptr, npair, w.D.ptr, ndet, active,
-                                                      bmap.ptr + b0, w.E.ptr);
-    CU_LAUNCH_CHECK();
+    if (emulated) {
+      contract_ozaki(ctx, bp.gp.ptr, npair, w.D.ptr, ndet, nb, active, bmap.ptr + b0, w.E.ptr,
+                     w.err.ptr);
+    } else {
+      k_contract_fp64<<<g2, 256, smem_c, ctx->stream>>>(bp.gp.ptr, npair, w.D.ptr, ndet, active,
+                                                        bmap.ptr + b0, w.E.ptr);
+      CU_LAUNCH_CHECK();
+    }
     ctx->fp64_timer.end(ctx->stream, ev);
     ctx->stats.fp64_launches += 1;
     k_scatter_fp64<<<g1, 256, 0, ctx->stream>>>(bp.tab->link.ptr, bp.tab->masks.ptr, bp.nstr,
-                                                bp.n, bp.nsig, w.E.ptr, c, c_stride, spin_shift,
+                                                bp.n, bp.nsig, w.E.ptr, emulated ? 1 : 0, c, c_stride, spin_shift,
                                                 active, bmap.ptr + b0, out, out_stride);
     CU_LAUNCH_CHECK();
   }

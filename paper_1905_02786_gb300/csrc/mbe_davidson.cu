@@ -1,5 +1,6 @@
 // Batched Davidson iteration (Davidson, J. Comput. Phys. 17, 87 (1975)) for
-// the lowest singlet of every CASCI of one bin, FP64 throughout:
+// the lowest singlet of every CASCI of one bin in the FP64 and emulated-FP64
+// modes (the mixed mode's Davidson is in mbe_davidson32.cu), FP64 throughout:
 //   K5  batched projections V^T w (two-phase, fixed-order reductions)
 //   K6  Rayleigh-Ritz: cyclic Jacobi on the m x m projected matrix, one warp
 //       per tuple
@@ -427,36 +428,6 @@ __global__ void k_guess(const double* __restrict__ hd, int nstr, int M, double* 
   }
 }
 
-// V[b][0] = X[b]
-__global__ void k_copy_x(const double* __restrict__ X, double* __restrict__ V, int M, int64_t N,
-                         const int32_t* __restrict__ active) {
-  const int b = blockIdx.y;
-  if (!active[b]) return;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N;
-       k += (int64_t)gridDim.x * blockDim.x)
-    V[(int64_t)b * M * N + k] = X[(int64_t)b * N + k];
-}
-
-// after an exact (FP64) sigma of x: keep refining tuples whose exact
-// residual is above target; the next mixed stage stops at a residual of
-// max(target, exact residual / 20)
-__global__ void k_refine_select(const double* __restrict__ rnorm, int B, double target,
-                                int32_t* __restrict__ active, double* __restrict__ tolr,
-                                int32_t* __restrict__ nactive) {
-  __shared__ int cnt;
-  if (threadIdx.x == 0) cnt = 0;
-  __syncthreads();
-  for (int b = threadIdx.x; b < B; b += blockDim.x) {
-    const double r = rnorm[b];
-    const int a = r > target ? 1 : 0;
-    active[b] = a;
-    tolr[b] = fmax(target, 0.05 * r);
-    if (a) atomicAdd(&cnt, 1);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) *nactive = cnt;
-}
-
 __global__ void k_fill(double* __restrict__ v, int n, double x) {
   for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = x;
 }
@@ -485,15 +456,8 @@ struct Multidot {
   }
 };
 
-// Davidson for one batch of tuples.
-//  FP64:  one stage with FP64 sigma vectors to conv_tol_r / conv_tol_e.
-//  mixed: stage A with tensor-core sigma vectors to a residual of 1e-3; then
-//         refinement rounds: an FP64 sigma of the current Ritz vector x gives
-//         the exact Rayleigh quotient and residual; tuples above conv_tol_r
-//         restart from {x} (with its exact A x) and continue with tensor-core
-//         sigma vectors for the correction directions, whose sigma errors
-//         scale with their small weights.  The last exact sigma provides the
-//         FP64 Rayleigh quotient that is reported.
+// Davidson for one batch of tuples: one stage with FP64 (or emulated-FP64)
+// sigma vectors to conv_tol_r / conv_tol_e.
 void davidson_batch(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int32_t* status_host,
                     double* s2_host, double* x_out_dev) {
   const int B = bp.B;
@@ -511,8 +475,10 @@ void davidson_batch(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int32_t* s
   SigmaWork sw;
   Multidot md;
   cudaStream_t st = ctx->stream;
-  const bool mixed =
-      ctx->opt.precision == MBE_MIXED_BF16X3 && sigma_tc_supported(bp.n, bp.nstr) && N > 1;
+  // sigma vectors: FP64 CUDA cores (MBE_FP64) or the FP64-grade sliced
+  // tensor-core contraction (MBE_EMULATED_FP64, and the mixed mode's
+  // fallback for spaces the fused tensor-core kernel does not cover)
+  const bool emulated = ctx->opt.precision != MBE_FP64 && ozaki_supported(bp.npair);
 
   launch_hdiag(ctx, bp, shift, hd.ptr);
   k_guess<<<B, 256, 0, st>>>(hd.ptr, bp.nstr, M, V.ptr);
@@ -521,8 +487,7 @@ void davidson_batch(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int32_t* s
   CU_LAUNCH_CHECK();
   CU_CHECK(cudaMemsetAsync(iters.ptr, 0, sizeof(int32_t) * B, st));
   CU_CHECK(cudaMemsetAsync(G.ptr, 0, sizeof(double) * B * M * M, st));
-  k_fill<<<1, 256, 0, st>>>(tolr.ptr, B, mixed ? std::max(ctx->opt.conv_tol_r, 1e-3)
-                                                : ctx->opt.conv_tol_r);
+  k_fill<<<1, 256, 0, st>>>(tolr.ptr, B, ctx->opt.conv_tol_r);
   CU_LAUNCH_CHECK();
 
   int64_t eblocks = std::min<int64_t>((N + 255) / 256, 1024);
@@ -533,9 +498,8 @@ void davidson_batch(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int32_t* s
   int64_t vecs_tc = 0, vecs_64 = 0;
   int total_it = 0;
 
-  auto sigma = [&](bool use_tc, const double* c, double* out) {
-    if (use_tc) sigma_tc(ctx, bp, sw, c, (int64_t)M * N, out, (int64_t)M * N, active.ptr, shift);
-    else sigma_fp64(ctx, bp, sw, c, (int64_t)M * N, out, (int64_t)M * N, active.ptr, shift);
+  auto sigma = [&](bool /*unused*/, const double* c, double* out) {
+    sigma_fp64(ctx, bp, sw, c, (int64_t)M * N, out, (int64_t)M * N, active.ptr, shift, emulated);
   };
   // precondition the residual in T, orthogonalise it against V[0..m) and
   // append it as V[m] (tuples whose correction vanished are frozen)
@@ -617,52 +581,9 @@ void davidson_batch(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int32_t* s
     }
   };
 
-  // exact (FP64) sigma of the current Ritz vectors x of all tuples: V0 = x,
-  // AV0 = A x, G = [[x.Ax]], theta, the exact residual (in T) and its norm
-  auto exact_point = [&]() {
-    k_set_i32<<<1, 256, 0, st>>>(active.ptr, B, 1);
-    CU_LAUNCH_CHECK();
-    k_copy_x<<<ge, 256, 0, st>>>(X, V.ptr, M, N, active.ptr);
-    CU_LAUNCH_CHECK();
-    sigma(false, V.ptr, AV.ptr);
-    vecs_64 += B;
-    md.run(ctx, V.ptr, (int64_t)M * N, N, AV.ptr, (int64_t)M * N, 1, N, B, active.ptr, coef.ptr,
-           M, 1);
-    k_store_grow<<<B, 32, 0, st>>>(coef.ptr, 1, M, active.ptr, G.ptr);
-    CU_LAUNCH_CHECK();
-    k_jacobi<<<B, 32, 0, st>>>(G.ptr, 1, M, active.ptr, theta.ptr, y.ptr);
-    CU_LAUNCH_CHECK();
-    k_residual<<<gc, 256, 0, st>>>(V.ptr, AV.ptr, 1, M, N, y.ptr, theta.ptr, active.ptr, X,
-                                   T.ptr, nchunks, rpart.ptr);
-    CU_LAUNCH_CHECK();
-    // residual norms only (the decision is k_refine_select's)
-    k_converge<<<1, 256, 0, st>>>(rpart.ptr, nchunks, B, 0, tolr.ptr, 0.0, 0, theta.ptr,
-                                  theta_old.ptr, rnorm.ptr, active.ptr, iters.ptr, nact.ptr);
-    CU_LAUNCH_CHECK();
-    k_save_yprev<<<B, 32, 0, st>>>(y.ptr, 1, M, 1, active.ptr, yp.ptr);
-    CU_LAUNCH_CHECK();
-  };
-
-  if (!mixed) {
-    stage(false, ctx->opt.conv_tol_e, 0, 1, max_iter, B, false);
-  } else {
-    // stage A: tensor-core sigma vectors to a residual of 1e-3 max(1, |theta|)
-    // (above the split-BF16x3 floor) or at most 150 iterations
-    stage(true, 1e300, 1, 1, 150, B, false);
-    // refinement rounds: exact residual, then a bounded tensor-core stage that
-    // reduces it by 20x (or to the target)
-    const double target = std::max(ctx->opt.conv_tol_r, 3e-8);
-    for (int round = 0; round < 12; round++) {
-      exact_point();
-      k_refine_select<<<1, 256, 0, st>>>(rnorm.ptr, B, target, active.ptr, tolr.ptr, nact.ptr);
-      CU_LAUNCH_CHECK();
-      const int na = count_active();
-      if (na == 0 || total_it >= max_iter) break;
-      extend(1);   // preconditioned exact residual becomes V_1
-      stage(true, 1e300, 0, 2, 40, na, true);
-    }
-    if (sigma_tc_error(ctx, sw)) throw MbeError{MBE_ECUDA, "tensor-core sigma wait timed out"};
-  }
+  stage(false, ctx->opt.conv_tol_e, 0, 1, max_iter, B, false);
+  if (emulated && sigma_tc_error(ctx, sw))
+    throw MbeError{MBE_ECUDA, "tensor-core contraction wait timed out"};
 
   // status and energies: eps = E_core + theta - shift <x|S^2|x> / <x|x>
   std::vector<int32_t> it_h(B);
@@ -683,7 +604,7 @@ void davidson_batch(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int32_t* s
     const double s2n = nx[b] > 0.0 ? s2[b] / nx[b] : 0.0;
     if (e_out_host) e_out_host[b] = ec[b] + th[b] - shift * s2n;
     if (s2_host) s2_host[b] = s2n;
-    bool ok = rn_h[b] <= (mixed ? std::max(rtol, 3e-8) : rtol) * 10.0 || N == 1;
+    bool ok = rn_h[b] <= rtol * 10.0 || N == 1;
     if (status_host) status_host[b] = ok ? MBE_OK : MBE_ENOCONV;
     ctx->stats.iters_total += it_h[b];
     ctx->stats.iters_max = std::max<int64_t>(ctx->stats.iters_max, it_h[b]);
@@ -693,6 +614,5 @@ void davidson_batch(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int32_t* s
   ctx->stats.casci += B;
   ctx->stats.sigma_vectors += vecs_tc + vecs_64;
   ctx->stats.sigma_flops += (double)(vecs_tc + vecs_64) * per;
-  ctx->stats.dom_flops += (double)vecs_tc * per;      // tensor-core sigma vectors
-  ctx->stats.fp64_flops += (double)vecs_64 * per;     // FP64 sigma vectors
+  ctx->stats.fp64_flops += (double)(vecs_tc + vecs_64) * per;   // exact sigma vectors
 }

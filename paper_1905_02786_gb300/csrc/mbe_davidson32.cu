@@ -1,0 +1,818 @@
+// Davidson iteration of the mixed-precision mode, laid out for GB300.
+//
+// GB300 issues FP64 arithmetic at roughly 1/60 of its FP32 rate, so every
+// per-determinant operation here is FP32: the subspace vectors V, their
+// sigma vectors AV, residuals and preconditioned corrections are stored and
+// combined in FP32, with per-thread FP32 partial sums reduced in FP64 across
+// threads.  FP64-grade quantities are formed only where the energy depends
+// on them, at "exact points":
+//   x      the current Ritz vector (FP32 values, taken as exact),
+//   A x    by the FP64-grade sliced tensor-core contraction,
+//   x.x    by an error-free FP32 dot (two-product + compensated sum),
+//   theta  = x.Ax / x.x, the Rayleigh quotient reported as the energy,
+//   r_x    = A x - theta x, its norm in FP64.
+// Iteration (Davidson, J. Comput. Phys. 17, 87 (1975)):
+//   stage A: tensor-core (split-BF16x3) sigma vectors until the residual is
+//            below 1e-3 max(1, |theta|) (above their precision floor);
+//   rounds:  exact point; tuples with |r_x| above the target continue from
+//            {x, t_1, ...} where t_j get tensor-core sigma vectors and the
+//            couplings x.A t_j = theta (x.t_j) + r_x.t_j use only exact data;
+//            the stage stops at max(target, |r_x| / 20).
+// The energy error of the reported Rayleigh quotient is below |r_x|^2 / gap.
+#include "mbe_internal.cuh"
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+
+namespace {
+
+constexpr int CH = 4096;     // elements per reduction chunk
+constexpr int RT = 256;      // threads of the reduction kernels
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int off = 16; off; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += red[w];
+  return s;
+}
+
+// partial[b][i][chunk] = sum over the chunk of X[b][i][k] Y[b][k], i < m
+__global__ void k32_multidot(const float* __restrict__ X, int64_t xb, int64_t xv,
+                             const float* __restrict__ Y, int64_t yb, int m, int64_t N, int nchunks,
+                             const int32_t* __restrict__ active, double* __restrict__ partial) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const int chunk = blockIdx.x;
+  const int64_t k0 = (int64_t)chunk * CH, k1 = min(N, k0 + CH);
+  __shared__ double red[32][33];
+  const float* y = Y + (int64_t)b * yb;
+  const float* x = X + (int64_t)b * xb;
+  for (int i0 = 0; i0 < m; i0 += 16) {
+    const int ni = min(16, m - i0);
+    float acc[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) acc[i] = 0.f;
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+      const float yv = y[k];
+#pragma unroll
+      for (int i = 0; i < 16; i++)
+        if (i < ni) acc[i] = fmaf(x[(int64_t)(i0 + i) * xv + k], yv, acc[i]);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+      double v = (double)acc[i];
+      for (int off = 16; off; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+      if (lane == 0) red[warp][i] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < ni) {
+      double s = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += red[w][threadIdx.x];
+      partial[((int64_t)b * m + i0 + threadIdx.x) * nchunks + chunk] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// error-free dot of two FP32 vectors: products split exactly (p + e = x y),
+// the p terms summed with compensation, all per-thread sums combined in FP64
+__global__ void k32_dot_comp(const float* __restrict__ X, int64_t xb, const float* __restrict__ Y,
+                             int64_t yb, int64_t N, int nchunks, const int32_t* __restrict__ active,
+                             double* __restrict__ partial) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  __shared__ double red[32];
+  const int64_t k0 = (int64_t)blockIdx.x * CH, k1 = min(N, k0 + CH);
+  const float* x = X + (int64_t)b * xb;
+  const float* y = Y + (int64_t)b * yb;
+  // (s, lo): s + lo carries the running sum to ~2^-48 relative; every
+  // product is split exactly (p + e = a b, fma) and every addition of p to s
+  // exactly (TwoSum: s + p = t + err)
+  float s = 0.f, lo = 0.f;
+  for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+    const float a = x[k], bb = y[k];
+    const float p = a * bb;
+    const float e = fmaf(a, bb, -p);
+    const float t = s + p;
+    const float bp = t - s;
+    const float err = (s - (t - bp)) + (p - bp);
+    s = t;
+    lo += err + e;
+  }
+  const double tot = block_sum((double)s + (double)lo, red);
+  if (threadIdx.x == 0) partial[(int64_t)b * nchunks + blockIdx.x] = tot;
+}
+
+__global__ void k32_final(const double* __restrict__ partial, int m, int nchunks,
+                          const int32_t* __restrict__ active, double* __restrict__ out, int64_t ob,
+                          int64_t oi) {
+  const int b = blockIdx.x;
+  if (active && !active[b]) return;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const double* p = partial + ((int64_t)b * m + i) * nchunks;
+    double s = 0.0;
+    for (int c = 0; c < nchunks; c++) s += p[c];
+    out[(int64_t)b * ob + (int64_t)i * oi] = s;
+  }
+}
+
+// G row j = m-1 from dots[b][i] (i < m); with exact0, entry 0 is replaced by
+// theta_x (x.t_j) + r_x.t_j  (cdot = x.t_j error-free, rdot = r_x.t_j)
+__global__ void k32_store_row(const double* __restrict__ dots, const double* __restrict__ cdot,
+                              const double* __restrict__ rdot, const double* __restrict__ thx,
+                              int m, int M, int exact0, const int32_t* __restrict__ active,
+                              double* __restrict__ G) {
+  const int b = blockIdx.x;
+  if (!active[b]) return;
+  const int j = m - 1;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    double v = dots[(int64_t)b * M + i];
+    if (exact0 && i == 0 && j > 0) v = thx[b] * cdot[b] + rdot[b];
+    G[(int64_t)b * M * M + (int64_t)j * M + i] = v;
+    G[(int64_t)b * M * M + (int64_t)i * M + j] = v;
+  }
+}
+
+// lowest eigenpair of the m x m symmetric G[b] by cyclic Jacobi (one warp)
+__global__ void k32_jacobi(const double* __restrict__ G, int m, int M,
+                           const int32_t* __restrict__ active, double* __restrict__ theta,
+                           double* __restrict__ y) {
+  const int b = blockIdx.x;
+  if (!active[b]) return;
+  __shared__ double A[32][33];
+  __shared__ double Z[32][33];
+  const int r = threadIdx.x;
+  for (int i = 0; i < m; i++)
+    if (r < m) {
+      A[i][r] = 0.5 * (G[(int64_t)b * M * M + (int64_t)i * M + r] +
+                       G[(int64_t)b * M * M + (int64_t)r * M + i]);
+      Z[i][r] = (i == r) ? 1.0 : 0.0;
+    }
+  __syncwarp();
+  for (int sweep = 0; sweep < 40; sweep++) {
+    double off = 0.0, dia = 0.0;
+    if (r < m)
+      for (int j = 0; j < m; j++) {
+        if (j != r) off += A[r][j] * A[r][j];
+        else dia += A[r][j] * A[r][j];
+      }
+    for (int o = 16; o; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      dia += __shfl_xor_sync(0xffffffffu, dia, o);
+    }
+    if (off <= 1e-30 * dia || off == 0.0) break;
+    for (int p = 0; p < m - 1; p++)
+      for (int q = p + 1; q < m; q++) {
+        const double apq = A[p][q];
+        if (fabs(apq) < 1e-300) continue;
+        const double app = A[p][p], aqq = A[q][q];
+        const double th = (aqq - app) / (2.0 * apq);
+        const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        __syncwarp();
+        double arp = 0.0, arq = 0.0, zrp = 0.0, zrq = 0.0;
+        if (r < m) { arp = A[r][p]; arq = A[r][q]; zrp = Z[r][p]; zrq = Z[r][q]; }
+        __syncwarp();
+        if (r < m) {
+          if (r != p && r != q) {
+            const double nrp = c * arp - s * arq, nrq = s * arp + c * arq;
+            A[r][p] = nrp; A[p][r] = nrp;
+            A[r][q] = nrq; A[q][r] = nrq;
+          }
+          Z[r][p] = c * zrp - s * zrq;
+          Z[r][q] = s * zrp + c * zrq;
+        }
+        __syncwarp();
+        if (r == 0) {
+          A[p][p] = app - t * apq;
+          A[q][q] = aqq + t * apq;
+          A[p][q] = 0.0;
+          A[q][p] = 0.0;
+        }
+        __syncwarp();
+      }
+  }
+  __syncwarp();
+  int k = 0;
+  double best = A[0][0];
+  for (int i = 1; i < m; i++)
+    if (A[i][i] < best) { best = A[i][i]; k = i; }
+  if (r == 0) theta[b] = best;
+  if (r < m) y[(int64_t)b * M + r] = Z[r][k];
+}
+
+// x = V y; r = AV y - theta x (stage A), or with exact0
+// r = y_0 (r_x + (theta_x - theta) V_0) + sum_{i>=1} y_i (AV_i - theta V_i)
+__global__ void k32_residual(const float* __restrict__ V, const float* __restrict__ AV,
+                             const float* __restrict__ RX, int exact0, int m, int M, int64_t N,
+                             const double* __restrict__ y, const double* __restrict__ theta,
+                             const double* __restrict__ thx, const int32_t* __restrict__ active,
+                             float* __restrict__ X, float* __restrict__ T, int nchunks,
+                             double* __restrict__ partial) {
+  const int b = blockIdx.y;
+  if (!active[b]) return;
+  __shared__ float sy[32];
+  __shared__ double red[32];
+  if (threadIdx.x < m) sy[threadIdx.x] = (float)y[(int64_t)b * M + threadIdx.x];
+  __syncthreads();
+  const float th = (float)theta[b];
+  const float dth = exact0 ? (float)(thx[b] - theta[b]) : 0.f;
+  const int64_t k0 = (int64_t)blockIdx.x * CH, k1 = min(N, k0 + CH);
+  const float* Vb = V + (int64_t)b * M * N;
+  const float* AVb = AV + (int64_t)b * M * N;
+  float acc = 0.f;
+  for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+    float x = 0.f, r = 0.f;
+    const int i0 = exact0 ? 1 : 0;
+    if (exact0) {
+      const float v0 = Vb[k];
+      x = sy[0] * v0;
+      r = sy[0] * (RX[(int64_t)b * N + k] + dth * v0);
+    }
+    for (int i = i0; i < m; i++) {
+      const float v = Vb[(int64_t)i * N + k];
+      x = fmaf(sy[i], v, x);
+      r = fmaf(sy[i], AVb[(int64_t)i * N + k] - th * v, r);
+    }
+    X[(int64_t)b * N + k] = x;
+    T[(int64_t)b * N + k] = r;
+    acc = fmaf(r, r, acc);
+  }
+  const double tot = block_sum((double)acc, red);
+  if (threadIdx.x == 0) partial[(int64_t)b * nchunks + blockIdx.x] = tot;
+}
+
+__global__ void k32_converge(const double* __restrict__ partial, int nchunks, int B, int it,
+                             const double* __restrict__ tol_r, int rel,
+                             const double* __restrict__ theta, double* __restrict__ rnorm,
+                             int32_t* __restrict__ active, int32_t* __restrict__ iters,
+                             int32_t* __restrict__ nactive) {
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    if (!active[b]) continue;
+    double s = 0.0;
+    for (int c = 0; c < nchunks; c++) s += partial[(int64_t)b * nchunks + c];
+    const double rn = sqrt(s);
+    rnorm[b] = rn;
+    iters[b] += 1;
+    const double tr = rel ? tol_r[b] * fmax(1.0, fabs(theta[b])) : tol_r[b];
+    if (it > 0 && rn < tr) active[b] = 0;
+    else atomicAdd(&cnt, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *nactive = cnt;
+}
+
+// t = r / (theta - H_II), symmetrised over (Ia, Ib) <-> (Ib, Ia)
+__global__ void k32_precondition(float* __restrict__ T, const float* __restrict__ hd, int nstr,
+                                 const double* __restrict__ theta,
+                                 const int32_t* __restrict__ active) {
+  const int b = blockIdx.y;
+  if (!active[b]) return;
+  const float th = (float)theta[b];
+  const int64_t N = (int64_t)nstr * nstr;
+  float* Tb = T + (int64_t)b * N;
+  const float* hb = hd + (int64_t)b * N;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int ia = (int)(k / nstr), ib = (int)(k % nstr);
+    if (ia > ib) continue;
+    const int64_t kt = (int64_t)ib * nstr + ia;
+    float d1 = th - hb[k], d2 = th - hb[kt];
+    if (fabsf(d1) < 1e-4f) d1 = d1 < 0.f ? -1e-4f : 1e-4f;
+    if (fabsf(d2) < 1e-4f) d2 = d2 < 0.f ? -1e-4f : 1e-4f;
+    const float t = 0.5f * (Tb[k] / d1 + Tb[kt] / d2);
+    Tb[k] = t;
+    Tb[kt] = t;
+  }
+}
+
+__global__ void k32_orth_axpy(float* __restrict__ T, const float* __restrict__ V, int m, int M,
+                              int64_t N, const double* __restrict__ coef,
+                              const int32_t* __restrict__ active) {
+  const int b = blockIdx.y;
+  if (!active[b]) return;
+  __shared__ float sc[32];
+  if (threadIdx.x < m) sc[threadIdx.x] = (float)coef[(int64_t)b * M + threadIdx.x];
+  __syncthreads();
+  const float* Vb = V + (int64_t)b * M * N;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    float t = T[(int64_t)b * N + k];
+    for (int i = 0; i < m; i++) t = fmaf(-sc[i], Vb[(int64_t)i * N + k], t);
+    T[(int64_t)b * N + k] = t;
+  }
+}
+
+__global__ void k32_append(const float* __restrict__ T, float* __restrict__ V, int m, int M,
+                           int64_t N, const double* __restrict__ nrm2,
+                           int32_t* __restrict__ active) {
+  const int b = blockIdx.y;
+  if (!active[b]) return;
+  const double n2 = nrm2[(int64_t)b * M];
+  if (!(n2 > 1e-24)) {
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0) active[b] = 2;
+    return;
+  }
+  const float inv = (float)(1.0 / sqrt(n2));
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N;
+       k += (int64_t)gridDim.x * blockDim.x)
+    V[(int64_t)b * M * N + (int64_t)m * N + k] = T[(int64_t)b * N + k] * inv;
+}
+
+__global__ void k32_fix_frozen(int32_t* active, int B) {
+  for (int b = threadIdx.x; b < B; b += blockDim.x)
+    if (active[b] == 2) active[b] = 0;
+}
+
+__global__ void k32_restart_coef(const double* __restrict__ y, double* __restrict__ yp, int m,
+                                 int M, const int32_t* __restrict__ active, double* __restrict__ G) {
+  const int b = blockIdx.x;
+  if (!active[b]) return;
+  __shared__ double sy[32], sq[32], sG[32][33];
+  const int r = threadIdx.x;
+  sy[r] = r < m ? y[(int64_t)b * M + r] : 0.0;
+  sq[r] = r < m ? yp[(int64_t)b * M + r] : 0.0;
+  for (int i = 0; i < m; i++)
+    if (r < m) sG[i][r] = G[(int64_t)b * M * M + (int64_t)i * M + r];
+  __syncwarp();
+  auto wsum = [](double v) {
+    for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+  };
+  for (int pass = 0; pass < 2; pass++) {
+    const double d = wsum(sy[r] * sq[r]);
+    sq[r] -= d * sy[r];
+    __syncwarp();
+  }
+  double nq = sqrt(wsum(sq[r] * sq[r]));
+  if (!(nq > 1e-14)) {
+    double a = r < m ? fabs(sy[r]) : 1e300;
+    int idx = r;
+    for (int off = 16; off; off >>= 1) {
+      const double oa = __shfl_xor_sync(0xffffffffu, a, off);
+      const int oi = __shfl_xor_sync(0xffffffffu, idx, off);
+      if (oa < a || (oa == a && oi < idx)) { a = oa; idx = oi; }
+    }
+    sq[r] = (r == idx) ? 1.0 : 0.0;
+    __syncwarp();
+    const double d = wsum(sy[r] * sq[r]);
+    sq[r] -= d * sy[r];
+    __syncwarp();
+    nq = sqrt(wsum(sq[r] * sq[r]));
+  }
+  sq[r] /= nq;
+  __syncwarp();
+  double gy = 0.0, gq = 0.0;
+  if (r < m)
+    for (int j = 0; j < m; j++) {
+      gy = fma(sG[r][j], sy[j], gy);
+      gq = fma(sG[r][j], sq[j], gq);
+    }
+  const double g00 = wsum(sy[r] * gy), g01 = wsum(sy[r] * gq), g11 = wsum(sq[r] * gq);
+  const double g10 = wsum(sq[r] * gy);
+  if (r < m) yp[(int64_t)b * M + r] = sq[r];
+  if (r == 0) {
+    double* Gb = G + (int64_t)b * M * M;
+    const double off = 0.5 * (g01 + g10);
+    Gb[0] = g00;
+    Gb[1] = off;
+    Gb[M] = off;
+    Gb[M + 1] = g11;
+  }
+}
+
+__global__ void k32_restart_vec(float* __restrict__ V, float* __restrict__ AV, int m, int M,
+                                int64_t N, const double* __restrict__ y,
+                                const double* __restrict__ q, const int32_t* __restrict__ active) {
+  const int b = blockIdx.y;
+  if (!active[b]) return;
+  __shared__ float sy[32], sq[32];
+  if (threadIdx.x < m) {
+    sy[threadIdx.x] = (float)y[(int64_t)b * M + threadIdx.x];
+    sq[threadIdx.x] = (float)q[(int64_t)b * M + threadIdx.x];
+  }
+  __syncthreads();
+  float* Vb = V + (int64_t)b * M * N;
+  float* AVb = AV + (int64_t)b * M * N;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    float x = 0.f, xp = 0.f, ax = 0.f, axp = 0.f;
+    for (int i = 0; i < m; i++) {
+      const float v = Vb[(int64_t)i * N + k], av = AVb[(int64_t)i * N + k];
+      x = fmaf(sy[i], v, x);
+      xp = fmaf(sq[i], v, xp);
+      ax = fmaf(sy[i], av, ax);
+      axp = fmaf(sq[i], av, axp);
+    }
+    Vb[k] = x;
+    Vb[N + k] = xp;
+    AVb[k] = ax;
+    AVb[N + k] = axp;
+  }
+}
+
+__global__ void k32_save_yprev(const double* __restrict__ y, int m, int M, int restarted,
+                               const int32_t* __restrict__ active, double* __restrict__ yp) {
+  const int b = blockIdx.x;
+  if (!active[b]) return;
+  for (int i = threadIdx.x; i < M; i += blockDim.x)
+    yp[(int64_t)b * M + i] =
+        restarted ? (i == 0 ? 1.0 : 0.0) : (i < m ? y[(int64_t)b * M + i] : 0.0);
+}
+
+__global__ void k32_guess(const float* __restrict__ hd, int nstr, int M, float* __restrict__ V) {
+  const int b = blockIdx.x;
+  const int64_t N = (int64_t)nstr * nstr;
+  __shared__ float sv[256];
+  __shared__ int64_t si[256];
+  float best = 3.4e38f;
+  int64_t bi = 0;
+  for (int64_t k = threadIdx.x; k < N; k += blockDim.x) {
+    const float v = hd[(int64_t)b * N + k];
+    if (v < best) { best = v; bi = k; }
+  }
+  sv[threadIdx.x] = best;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s; s >>= 1) {
+    if (threadIdx.x < s) {
+      const float o = sv[threadIdx.x + s];
+      const int64_t oi = si[threadIdx.x + s];
+      if (o < sv[threadIdx.x] || (o == sv[threadIdx.x] && oi < si[threadIdx.x])) {
+        sv[threadIdx.x] = o;
+        si[threadIdx.x] = oi;
+      }
+    }
+    __syncthreads();
+  }
+  float* Vb = V + (int64_t)b * M * N;
+  for (int64_t k = threadIdx.x; k < N; k += blockDim.x) Vb[k] = 0.f;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int64_t i0 = si[0];
+    const int ia = (int)(i0 / nstr), ib = (int)(i0 % nstr);
+    if (ia == ib) Vb[i0] = 1.f;
+    else {
+      Vb[(int64_t)ia * nstr + ib] = 0.70710678f;
+      Vb[(int64_t)ib * nstr + ia] = 0.70710678f;
+    }
+  }
+}
+
+__global__ void k32_from_f64(const double* __restrict__ src, float* __restrict__ dst, int64_t n) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    dst[k] = (float)src[k];
+}
+
+// V0 = X / |X| (FP32) and its FP64 copy C64 (input of the exact sigma)
+__global__ void k32_exact_prep(const float* __restrict__ X, const double* __restrict__ xx,
+                               float* __restrict__ V, int M, double* __restrict__ C64, int64_t N,
+                               const int32_t* __restrict__ active) {
+  const int b = blockIdx.y;
+  if (!active[b]) return;
+  const float inv = (float)(1.0 / sqrt(xx[b]));
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const float v = X[(int64_t)b * N + k] * inv;
+    V[(int64_t)b * M * N + k] = v;
+    C64[(int64_t)b * N + k] = (double)v;
+  }
+}
+
+// partial sums of V0 . A V0 in FP64 (one FP64 FMA per element)
+__global__ void k32_exact_xax(const double* __restrict__ C64, const double* __restrict__ S64,
+                              int64_t N, int nchunks, const int32_t* __restrict__ active,
+                              double* __restrict__ partial) {
+  const int b = blockIdx.y;
+  if (!active[b]) return;
+  __shared__ double red[32];
+  const int64_t k0 = (int64_t)blockIdx.x * CH, k1 = min(N, k0 + CH);
+  double acc = 0.0;
+  for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x)
+    acc = fma(C64[(int64_t)b * N + k], S64[(int64_t)b * N + k], acc);
+  const double tot = block_sum(acc, red);
+  if (threadIdx.x == 0) partial[(int64_t)b * nchunks + blockIdx.x] = tot;
+}
+
+// r_x = A V0 - theta_x V0 (stored FP32) and partial sums of |r_x|^2
+__global__ void k32_exact_rx(const double* __restrict__ C64, const double* __restrict__ S64,
+                             const double* __restrict__ thx, int64_t N, int nchunks,
+                             const int32_t* __restrict__ active, float* __restrict__ RX,
+                             double* __restrict__ partial) {
+  const int b = blockIdx.y;
+  if (!active[b]) return;
+  __shared__ double red[32];
+  const double th = thx[b];
+  const int64_t k0 = (int64_t)blockIdx.x * CH, k1 = min(N, k0 + CH);
+  double acc = 0.0;
+  for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+    const double r = fma(-th, C64[(int64_t)b * N + k], S64[(int64_t)b * N + k]);
+    RX[(int64_t)b * N + k] = (float)r;
+    acc = fma(r, r, acc);
+  }
+  const double tot = block_sum(acc, red);
+  if (threadIdx.x == 0) partial[(int64_t)b * nchunks + blockIdx.x] = tot;
+}
+
+// theta_x = xAx / xx; G = [[xAx]]; rnorm from the partials; y = [1]
+__global__ void k32_exact_fin(const double* __restrict__ xax, const double* __restrict__ xx,
+                              const double* __restrict__ rpart, int nchunks, int M, int B,
+                              const int32_t* __restrict__ active, double* __restrict__ thx,
+                              double* __restrict__ theta, double* __restrict__ G,
+                              double* __restrict__ rnorm, int32_t* __restrict__ iters) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+    if (!active[b]) continue;
+    const double t = xax[b] / xx[b];
+    thx[b] = t;
+    theta[b] = t;
+    G[(int64_t)b * M * M] = xax[b];
+    double s = 0.0;
+    for (int c = 0; c < nchunks; c++) s += rpart[(int64_t)b * nchunks + c];
+    rnorm[b] = sqrt(s);
+    iters[b] += 1;
+  }
+}
+
+// target of tuple b: max(abs_target, rel_target max(1, |theta_x|)); the FP32
+// storage of x puts a floor of a few 1e-8 |A| on its exact residual
+__global__ void k32_select(const double* __restrict__ rnorm, const int32_t* __restrict__ mask,
+                           const double* __restrict__ thx, int B, double abs_target,
+                           double rel_target, int32_t* __restrict__ active,
+                           double* __restrict__ tolr, int32_t* __restrict__ nactive) {
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    const double target = fmax(abs_target, rel_target * fmax(1.0, fabs(thx[b])));
+    const int a = (mask[b] && rnorm[b] > target) ? 1 : 0;
+    active[b] = a;
+    tolr[b] = fmax(target, 0.05 * rnorm[b]);
+    if (a) atomicAdd(&cnt, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *nactive = cnt;
+}
+
+__global__ void k32_fill_i(int32_t* v, int n, int32_t x) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = x;
+}
+__global__ void k32_fill_d(double* v, int n, double x) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = x;
+}
+__global__ void k32_copy_i(const int32_t* s, int32_t* d, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = s[i];
+}
+
+}  // namespace
+
+void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int32_t* status_host,
+                          double* x_out_dev) {
+  const int B = bp.B;
+  const int M = std::max(4, std::min(32, ctx->opt.max_subspace));
+  const int64_t N = bp.ndet;
+  const double shift = ctx->opt.spin_shift;
+  DevPool* P = &ctx->pool;
+  const int nchunks = (int)((N + CH - 1) / CH);
+  DevBuf<float> V(P, (size_t)B * M * N), AV(P, (size_t)B * M * N), hd(P, (size_t)B * N),
+      T(P, (size_t)B * N), X(P, (size_t)B * N), RX(P, (size_t)B * N);
+  DevBuf<double> hd64(P, (size_t)B * N), C64(P, (size_t)B * N), S64(P, (size_t)B * N),
+      G(P, (size_t)B * M * M), y(P, (size_t)B * M), yp(P, (size_t)B * M), theta(P, B),
+      thx(P, B), rnorm(P, B), tolr(P, B), coef(P, (size_t)B * M), cdot(P, B), rdot(P, B),
+      xx(P, B), xax(P, B), partial(P, (size_t)B * M * nchunks), rpart(P, (size_t)B * nchunks);
+  DevBuf<int32_t> active(P, B), iters(P, B), nact(P, 1), mask(P, B);
+  SigmaWork sw;
+  cudaStream_t st = ctx->stream;
+  const int64_t eb = std::min<int64_t>((N + 255) / 256, 1024);
+  const dim3 ge((unsigned)eb, B), gc(nchunks, B);
+  const int max_iter = std::max(1, ctx->opt.max_iter);
+  int total_it = 0;
+  int64_t vecs_tc = 0, vecs_ex = 0;
+
+  // diagonal (FP64 kernel shared with the FP64 mode), kept in FP32
+  launch_hdiag(ctx, bp, shift, hd64.ptr);
+  k32_from_f64<<<ge.x, 256, 0, st>>>(hd64.ptr, hd.ptr, (int64_t)B * N);
+  CU_LAUNCH_CHECK();
+  k32_guess<<<B, 256, 0, st>>>(hd.ptr, bp.nstr, M, V.ptr);
+  CU_LAUNCH_CHECK();
+  k32_fill_i<<<1, 256, 0, st>>>(active.ptr, B, 1);
+  CU_LAUNCH_CHECK();
+  CU_CHECK(cudaMemsetAsync(iters.ptr, 0, sizeof(int32_t) * B, st));
+  CU_CHECK(cudaMemsetAsync(G.ptr, 0, sizeof(double) * B * M * M, st));
+  k32_fill_d<<<1, 256, 0, st>>>(tolr.ptr, B, 1e-3);
+  CU_LAUNCH_CHECK();
+
+  auto dots = [&](const float* Xv, int64_t xb, int64_t xv, const float* Yv, int64_t yb, int m,
+                  double* out, int64_t ob, int64_t oi, const int32_t* act) {
+    k32_multidot<<<dim3(nchunks, B), RT, 0, st>>>(Xv, xb, xv, Yv, yb, m, N, nchunks, act,
+                                                   partial.ptr);
+    CU_LAUNCH_CHECK();
+    k32_final<<<B, 32, 0, st>>>(partial.ptr, m, nchunks, act, out, ob, oi);
+    CU_LAUNCH_CHECK();
+  };
+  auto dot_comp = [&](const float* Xv, int64_t xb, const float* Yv, int64_t yb, double* out,
+                      const int32_t* act) {
+    k32_dot_comp<<<dim3(nchunks, B), RT, 0, st>>>(Xv, xb, Yv, yb, N, nchunks, act, partial.ptr);
+    CU_LAUNCH_CHECK();
+    k32_final<<<B, 32, 0, st>>>(partial.ptr, 1, nchunks, act, out, 1, 1);
+    CU_LAUNCH_CHECK();
+  };
+  auto count_active = [&]() {
+    int32_t n = 0;
+    CU_CHECK(cudaMemcpyAsync(&n, nact.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CU_CHECK(cudaStreamSynchronize(st));
+    if (ctx->opt.verbose) {
+      std::vector<double> rn(B), th(B);
+      CU_CHECK(cudaMemcpy(rn.data(), rnorm.ptr, sizeof(double) * B, cudaMemcpyDeviceToHost));
+      CU_CHECK(cudaMemcpy(th.data(), theta.ptr, sizeof(double) * B, cudaMemcpyDeviceToHost));
+      double mx = 0.0;
+      for (double r : rn) mx = std::max(mx, r);
+      fprintf(stderr, "[mbe mixed] n=%d nsig=%d B=%d it=%d active=%d max|r|=%.3e theta0=%.12f\n",
+              bp.n, bp.nsig, B, total_it, n, mx, th[0]);
+    }
+    return n;
+  };
+  // precondition T, orthogonalise against V[0..m) twice, append as V[m]
+  auto extend = [&](int m) {
+    k32_precondition<<<ge, 256, 0, st>>>(T.ptr, hd.ptr, bp.nstr, theta.ptr, active.ptr);
+    CU_LAUNCH_CHECK();
+    for (int pass = 0; pass < 2; pass++) {
+      dots(V.ptr, (int64_t)M * N, N, T.ptr, N, m, coef.ptr, M, 1, active.ptr);
+      k32_orth_axpy<<<ge, 256, 0, st>>>(T.ptr, V.ptr, m, M, N, coef.ptr, active.ptr);
+      CU_LAUNCH_CHECK();
+    }
+    dots(T.ptr, N, 0, T.ptr, N, 1, coef.ptr, M, 1, active.ptr);
+    k32_append<<<ge, 256, 0, st>>>(T.ptr, V.ptr, m, M, N, coef.ptr, active.ptr);
+    CU_LAUNCH_CHECK();
+    k32_fix_frozen<<<1, 256, 0, st>>>(active.ptr, B);
+    CU_LAUNCH_CHECK();
+  };
+  // Davidson iterations from a subspace of m_start vectors, the newest one's
+  // sigma pending; exact0: V_0 is an exact point (no restart: the stage ends
+  // when the subspace is full)
+  auto stage = [&](int m_start, int cap, int rel, bool exact0, int nact0) {
+    int m = m_start, nact_h = nact0;
+    for (int it = 0; it < cap && total_it < max_iter; it++, total_it++) {
+      sigma_tc(ctx, bp, sw, V.ptr + (int64_t)(m - 1) * N, (int64_t)M * N,
+               AV.ptr + (int64_t)(m - 1) * N, (int64_t)M * N, active.ptr, shift);
+      vecs_tc += nact_h;
+      dots(V.ptr, (int64_t)M * N, N, AV.ptr + (int64_t)(m - 1) * N, (int64_t)M * N, m, coef.ptr,
+           M, 1, active.ptr);
+      if (exact0) {
+        dot_comp(V.ptr, (int64_t)M * N, V.ptr + (int64_t)(m - 1) * N, (int64_t)M * N, cdot.ptr,
+                 active.ptr);
+        dots(RX.ptr, N, 0, V.ptr + (int64_t)(m - 1) * N, (int64_t)M * N, 1, rdot.ptr, 1, 1,
+             active.ptr);
+      }
+      k32_store_row<<<B, 32, 0, st>>>(coef.ptr, cdot.ptr, rdot.ptr, thx.ptr, m, M, exact0 ? 1 : 0,
+                                      active.ptr, G.ptr);
+      CU_LAUNCH_CHECK();
+      k32_jacobi<<<B, 32, 0, st>>>(G.ptr, m, M, active.ptr, theta.ptr, y.ptr);
+      CU_LAUNCH_CHECK();
+      k32_residual<<<gc, RT, 0, st>>>(V.ptr, AV.ptr, RX.ptr, exact0 ? 1 : 0, m, M, N, y.ptr,
+                                      theta.ptr, thx.ptr, active.ptr, X.ptr, T.ptr, nchunks,
+                                      rpart.ptr);
+      CU_LAUNCH_CHECK();
+      k32_converge<<<1, 256, 0, st>>>(rpart.ptr, nchunks, B, m_start > 1 ? it + 1 : it, tolr.ptr,
+                                      rel, theta.ptr, rnorm.ptr, active.ptr, iters.ptr, nact.ptr);
+      CU_LAUNCH_CHECK();
+      nact_h = count_active();
+      if (nact_h == 0) return;
+      if (exact0 && m == M) return;
+      int restarted = 0;
+      if (m == M) {
+        k32_restart_coef<<<B, 32, 0, st>>>(y.ptr, yp.ptr, m, M, active.ptr, G.ptr);
+        CU_LAUNCH_CHECK();
+        k32_restart_vec<<<ge, 256, 0, st>>>(V.ptr, AV.ptr, m, M, N, y.ptr, yp.ptr, active.ptr);
+        CU_LAUNCH_CHECK();
+        m = 2;
+        restarted = 1;
+      }
+      k32_save_yprev<<<B, 32, 0, st>>>(y.ptr, m, M, restarted, active.ptr, yp.ptr);
+      CU_LAUNCH_CHECK();
+      extend(m);
+      m++;
+    }
+  };
+  // exact point of the tuples in `mask`: V0 = x/|x|, exact A V0, theta_x,
+  // r_x and its norm; G = [[V0.AV0]]
+  auto exact_point = [&]() {
+    k32_copy_i<<<1, 256, 0, st>>>(mask.ptr, active.ptr, B);
+    CU_LAUNCH_CHECK();
+    dot_comp(X.ptr, N, X.ptr, N, xx.ptr, active.ptr);
+    k32_exact_prep<<<ge, 256, 0, st>>>(X.ptr, xx.ptr, V.ptr, M, C64.ptr, N, active.ptr);
+    CU_LAUNCH_CHECK();
+    dot_comp(V.ptr, (int64_t)M * N, V.ptr, (int64_t)M * N, xx.ptr, active.ptr);
+    sigma_fp64(ctx, bp, sw, C64.ptr, N, S64.ptr, N, active.ptr, shift, true);
+    vecs_ex += B;
+    k32_exact_xax<<<gc, RT, 0, st>>>(C64.ptr, S64.ptr, N, nchunks, active.ptr, rpart.ptr);
+    CU_LAUNCH_CHECK();
+    k32_final<<<B, 32, 0, st>>>(rpart.ptr, 1, nchunks, active.ptr, xax.ptr, 1, 1);
+    CU_LAUNCH_CHECK();
+    // theta_x first (the residual needs it), then r_x and its norm
+    k32_exact_fin<<<(B + 127) / 128, 128, 0, st>>>(xax.ptr, xx.ptr, rpart.ptr, 0, M, B,
+                                                   active.ptr, thx.ptr, theta.ptr, G.ptr,
+                                                   rnorm.ptr, iters.ptr);
+    CU_LAUNCH_CHECK();
+    k32_exact_rx<<<gc, RT, 0, st>>>(C64.ptr, S64.ptr, thx.ptr, N, nchunks, active.ptr, RX.ptr,
+                                    rpart.ptr);
+    CU_LAUNCH_CHECK();
+    k32_final<<<B, 32, 0, st>>>(rpart.ptr, 1, nchunks, active.ptr, rnorm.ptr, 1, 1);
+    CU_LAUNCH_CHECK();
+  };
+
+  // stage A
+  stage(1, 150, 1, false, B);
+  // refinement rounds
+  const double abs_target = ctx->opt.conv_tol_r, rel_target = 2e-7;
+  k32_fill_i<<<1, 256, 0, st>>>(mask.ptr, B, 1);
+  CU_LAUNCH_CHECK();
+  std::vector<double> rn2(B);
+  for (int round = 0; round < 12; round++) {
+    exact_point();
+    // rnorm holds |r_x|^2 sums: take the square root on the host side copy
+    CU_CHECK(cudaMemcpyAsync(rn2.data(), rnorm.ptr, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+    CU_CHECK(cudaStreamSynchronize(st));
+    std::vector<int32_t> mk(B);
+    CU_CHECK(cudaMemcpy(mk.data(), mask.ptr, sizeof(int32_t) * B, cudaMemcpyDeviceToHost));
+    for (int b = 0; b < B; b++)
+      if (mk[b]) rn2[b] = std::sqrt(std::max(0.0, rn2[b]));
+    CU_CHECK(cudaMemcpyAsync(rnorm.ptr, rn2.data(), sizeof(double) * B, cudaMemcpyHostToDevice, st));
+    k32_select<<<1, 256, 0, st>>>(rnorm.ptr, mask.ptr, thx.ptr, B, abs_target, rel_target,
+                                  active.ptr, tolr.ptr, nact.ptr);
+    CU_LAUNCH_CHECK();
+    const int na = count_active();
+    if (ctx->opt.verbose) {
+      double t0 = 0.0;
+      CU_CHECK(cudaMemcpy(&t0, thx.ptr, sizeof(double), cudaMemcpyDeviceToHost));
+      fprintf(stderr, "[mbe mixed] exact point %d: %d above target; theta_x0=%.15f |r_x0|=%.3e\n",
+              round, na, t0, rn2[0]);
+    }
+    if (na == 0 || total_it >= max_iter) break;
+    k32_copy_i<<<1, 256, 0, st>>>(active.ptr, mask.ptr, B);
+    CU_LAUNCH_CHECK();
+    // the exact residual, preconditioned, is the first correction
+    CU_CHECK(cudaMemcpyAsync(T.ptr, RX.ptr, sizeof(float) * B * N, cudaMemcpyDeviceToDevice, st));
+    k32_save_yprev<<<B, 32, 0, st>>>(y.ptr, 1, M, 1, active.ptr, yp.ptr);
+    CU_LAUNCH_CHECK();
+    extend(1);
+    stage(2, 40, 0, true, na);
+  }
+  if (sigma_tc_error(ctx, sw)) throw MbeError{MBE_ECUDA, "tensor-core sigma wait timed out"};
+
+  // energies: E = E_core + theta_x - shift <S^2> (S^2 of the exact-point vector, FP64)
+  s2_apply(ctx, bp, C64.ptr, N, S64.ptr, N, nullptr);
+  std::vector<double> th(B), ec(B), rn(B), s2(B), nx(B);
+  std::vector<int32_t> it_h(B);
+  {
+    // <S^2> = C64.S64 / C64.C64 via the FP64 partial-sum kernel
+    DevBuf<int32_t> all(P, B);
+    k32_fill_i<<<1, 256, 0, st>>>(all.ptr, B, 1);
+    CU_LAUNCH_CHECK();
+    k32_exact_xax<<<gc, RT, 0, st>>>(C64.ptr, S64.ptr, N, nchunks, all.ptr, rpart.ptr);
+    CU_LAUNCH_CHECK();
+    k32_final<<<B, 32, 0, st>>>(rpart.ptr, 1, nchunks, all.ptr, coef.ptr, 1, 1);
+    CU_LAUNCH_CHECK();
+    k32_exact_xax<<<gc, RT, 0, st>>>(C64.ptr, C64.ptr, N, nchunks, all.ptr, rpart.ptr);
+    CU_LAUNCH_CHECK();
+    k32_final<<<B, 32, 0, st>>>(rpart.ptr, 1, nchunks, all.ptr, xax.ptr, 1, 1);
+    CU_LAUNCH_CHECK();
+  }
+  CU_CHECK(cudaMemcpyAsync(th.data(), thx.ptr, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+  CU_CHECK(cudaMemcpyAsync(ec.data(), bp.ecore.ptr, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+  CU_CHECK(cudaMemcpyAsync(rn.data(), rnorm.ptr, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+  CU_CHECK(cudaMemcpyAsync(s2.data(), coef.ptr, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+  CU_CHECK(cudaMemcpyAsync(nx.data(), xax.ptr, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+  CU_CHECK(cudaMemcpyAsync(it_h.data(), iters.ptr, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, st));
+  if (x_out_dev)
+    CU_CHECK(cudaMemcpyAsync(x_out_dev, C64.ptr, sizeof(double) * B * N, cudaMemcpyDeviceToDevice, st));
+  CU_CHECK(cudaStreamSynchronize(st));
+
+  for (int b = 0; b < B; b++) {
+    const double s2n = nx[b] > 0.0 ? s2[b] / nx[b] : 0.0;
+    if (ctx->opt.verbose)
+      fprintf(stderr, "[mbe mixed] tuple %d: theta_x=%.15f <S^2>=%.3e |r_x|=%.3e E_core=%.12f\n", b,
+              th[b], s2n, rn[b], ec[b]);
+    if (e_out_host) e_out_host[b] = ec[b] + th[b] - shift * s2n;
+    const bool ok = rn[b] <= 10.0 * std::max(abs_target, rel_target * std::max(1.0, std::fabs(th[b])));
+    if (status_host) status_host[b] = ok ? MBE_OK : MBE_ENOCONV;
+    ctx->stats.iters_total += it_h[b];
+    ctx->stats.iters_max = std::max<int64_t>(ctx->stats.iters_max, it_h[b]);
+    ctx->stats.noconv += ok ? 0 : 1;
+  }
+  const double per = 2.0 * (double)N * bp.npair * bp.npair;
+  ctx->stats.casci += B;
+  ctx->stats.sigma_vectors += vecs_tc + vecs_ex;
+  ctx->stats.sigma_flops += (double)(vecs_tc + vecs_ex) * per;
+  ctx->stats.dom_flops += (double)vecs_tc * per;
+  ctx->stats.fp64_flops += (double)vecs_ex * per;
+}

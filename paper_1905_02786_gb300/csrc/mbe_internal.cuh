@@ -210,12 +210,21 @@ struct SigmaWork {
   int64_t sub_batch = 0;
 };
 bool sigma_tc_supported(int n, int nstr);
-void sigma_tc(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const double* c, int64_t c_stride,
-              double* out, int64_t out_stride, const int32_t* active, double spin_shift);
+// FP32 vectors in and out (c = c^T assumed: sigma = X + X^T)
+void sigma_tc(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const float* c, int64_t c_stride,
+              float* out, int64_t out_stride, const int32_t* active, double spin_shift);
 int32_t sigma_tc_error(mbe_ctx* ctx, SigmaWork& w);
+// Davidson of the mixed-precision mode: FP32 vectors, FP64-grade exact points
+void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host,
+                          int32_t* status_host, double* x_out_dev);
+// emulated: the contraction runs as the FP64-grade sliced tensor-core GEMM
 void sigma_fp64(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const double* c,
                 int64_t c_stride, double* out, int64_t out_stride,
-                const int32_t* active, double spin_shift);
+                const int32_t* active, double spin_shift, bool emulated);
+bool ozaki_supported(int npair);
+void contract_ozaki(mbe_ctx* ctx, const double* gp, int npair, const double* D, int64_t ndet,
+                    int nb, const int32_t* active, const int32_t* bmap, double* E,
+                    int32_t* err);
 void s2_apply(mbe_ctx* ctx, BinProblem& bp, const double* c, int64_t c_stride,
               double* out, int64_t out_stride, const int32_t* active);
 

@@ -22,8 +22,10 @@
 //      1/2 s E_P(a,k) into X(a, J) for the string J linked to k by P
 //      (shared-memory atomics).
 // Precision: both operands carry ~16 significant bits after the hi/lo split,
-// the dropped lo*lo term and the FP32 accumulation give sigma to ~1e-5
-// relative; the Davidson iteration corrects this with FP64 sigma vectors.
+// the dropped lo*lo term and the FP32 accumulation give sigma to ~1e-4 of
+// its largest element; the Davidson iteration corrects this with FP64-grade
+// sigma vectors.  Input c and output sigma are FP32 (no FP64 arithmetic on
+// the per-element path: GB300's FP64 pipe is a small fraction of FP32).
 #include "mbe_internal.cuh"
 #include <cuda_bf16.h>
 #include <algorithm>
@@ -147,7 +149,7 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bflo
 // One CTA = tuple b (blockIdx.y) x rows [a0, a0 + R) (blockIdx.x).
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad, int R,
-           const double* __restrict__ gp_all, const double* __restrict__ c, int64_t c_stride,
+           const double* __restrict__ gp_all, const float* __restrict__ c, int64_t c_stride,
            const int32_t* __restrict__ active, float* __restrict__ X, int64_t x_stride,
            int32_t* __restrict__ err) {
   const int b = blockIdx.y;
@@ -167,7 +169,7 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad, int 
   float* sX = (float*)(smem + L.x_rows);
   int32_t* sLk = (int32_t*)(smem + L.link_k);     // [P][W + 1]
   int32_t* sLa = (int32_t*)(smem + L.link_a);     // [r][P]
-  const double* cb = c + (int64_t)b * c_stride;
+  const float* cb = c + (int64_t)b * c_stride;
   const int64_t N = (int64_t)nstr * nstr;
 
   // ---- setup: g' split into bf16 hi/lo (rows >= npair and K >= npair zero)
@@ -191,7 +193,7 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad, int 
   for (int it = tid; it < R * nstr; it += TC_THREADS) {
     const int r = it / nstr, k = it % nstr;
     const int a = a0 + r;
-    sC[it] = a < nstr ? (float)cb[(int64_t)a * nstr + k] : 0.f;
+    sC[it] = a < nstr ? cb[(int64_t)a * nstr + k] : 0.f;
     sX[it] = 0.f;
   }
   for (int it = tid; it < R * npair; it += TC_THREADS) {
@@ -239,7 +241,7 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad, int 
         if (P < npair && a < nstr && k < nstr) {
           const int32_t ta = sLa[r * npair + P];
           if (ta >= 0) {
-            float x = (float)cb[(int64_t)(ta >> 1) * nstr + k];
+            float x = cb[(int64_t)(ta >> 1) * nstr + k];
             v += (ta & 1) ? -x : x;
           }
           const int32_t tk = sLk[P * (W + 1) + j];
@@ -314,12 +316,12 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad, int 
   (void)N;
 }
 
-// sigma(a,b) = X(a,b) + X(b,a) + shift (S^2 c)(a,b), FP64 output
+// sigma(a,b) = X(a,b) + X(b,a) + shift (S^2 c)(a,b), FP32 output
 __global__ void k_sigma_tc_finish(const float* __restrict__ X, int64_t x_stride,
                                   const int32_t* __restrict__ link, const uint32_t* __restrict__ masks,
-                                  int nstr, int n, int nsig, const double* __restrict__ c,
-                                  int64_t c_stride, double shift, const int32_t* __restrict__ active,
-                                  double* __restrict__ out, int64_t out_stride) {
+                                  int nstr, int n, int nsig, const float* __restrict__ c,
+                                  int64_t c_stride, float shift, const int32_t* __restrict__ active,
+                                  float* __restrict__ out, int64_t out_stride) {
   const int b = blockIdx.z;
   if (active && !active[b]) return;
   // 32 x 32 tile with its transpose staged in shared memory
@@ -332,26 +334,31 @@ __global__ void k_sigma_tc_finish(const float* __restrict__ X, int64_t x_stride,
   }
   __syncthreads();
   const int npair = n * (n + 1) / 2;
-  const double* cb = c + (int64_t)b * c_stride;
-  double* ob = out + (int64_t)b * out_stride;
+  const float* cb = c + (int64_t)b * c_stride;
+  float* ob = out + (int64_t)b * out_stride;
   for (int i = threadIdx.y; i < 32; i += blockDim.y) {
     const int ia = by + i, ib = bx + threadIdx.x;       // output (ia, ib): X(ia,ib) + X(ib,ia)
     if (ia >= nstr || ib >= nstr) continue;
     const int64_t idx = (int64_t)ia * nstr + ib;
-    double v = (double)Xb[idx] + (double)tT[i][threadIdx.x];
-    if (shift != 0.0) {
+    float v = Xb[idx] + tT[i][threadIdx.x];
+    if (shift != 0.f) {
       const int32_t* la = link + (int64_t)ia * npair;
       const int32_t* lb = link + (int64_t)ib * npair;
-      uint32_t ma = masks[ia], mb = masks[ib];
-      double s2 = (double)(nsig - __popc(ma & mb)) * cb[idx];
-      uint32_t oa = ma & ~mb, obm = mb & ~ma;
-      for (int q = 0; q < n; q++) {
-        if (!((oa >> q) & 1)) continue;
-        for (int p = 0; p < n; p++) {
-          if (!((obm >> p) & 1)) continue;
-          int P = p > q ? p * (p + 1) / 2 + q : q * (q + 1) / 2 + p;
-          int32_t ta = la[P], tb = lb[P];
-          double x = cb[(int64_t)(ta >> 1) * nstr + (tb >> 1)];
+      const uint32_t ma = masks[ia], mb = masks[ib];
+      float s2 = (float)(nsig - __popc(ma & mb)) * cb[idx];
+      // pairs {p, q}: q open in the alpha string, p open in the beta string
+      uint32_t oa = ma & ~mb;
+      const uint32_t obm = mb & ~ma;
+      while (oa) {
+        const int q = __ffs(oa) - 1;
+        oa &= oa - 1;
+        uint32_t ob2 = obm;
+        while (ob2) {
+          const int p = __ffs(ob2) - 1;
+          ob2 &= ob2 - 1;
+          const int P = p > q ? p * (p + 1) / 2 + q : q * (q + 1) / 2 + p;
+          const int32_t ta = la[P], tb = lb[P];
+          const float x = cb[(int64_t)(ta >> 1) * nstr + (tb >> 1)];
           s2 -= ((ta ^ tb) & 1) ? -x : x;
         }
       }
@@ -372,8 +379,8 @@ bool sigma_tc_supported(int n, int nstr) {
   return L.total + 2048 <= 227 * 1024;
 }
 
-void sigma_tc(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const double* c, int64_t c_stride,
-              double* out, int64_t out_stride, const int32_t* active, double spin_shift) {
+void sigma_tc(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const float* c, int64_t c_stride,
+              float* out, int64_t out_stride, const int32_t* active, double spin_shift) {
   const int npair = bp.npair, nstr = bp.nstr;
   const int kpad = ((npair + 15) / 16) * 16;
   const int R = nstr <= 2048 ? 2 : 1;
@@ -402,7 +409,7 @@ void sigma_tc(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const double* c, int64
   dim3 g2((unsigned)((nstr + 31) / 32), (unsigned)((nstr + 31) / 32), bp.B);
   k_sigma_tc_finish<<<g2, dim3(32, 8), 0, ctx->stream>>>(w.Xf.ptr, N, bp.tab->link.ptr,
                                                          bp.tab->masks.ptr, nstr, bp.n, bp.nsig, c,
-                                                         c_stride, spin_shift, active, out,
+                                                         c_stride, (float)spin_shift, active, out,
                                                          out_stride);
   CU_LAUNCH_CHECK();
 }
