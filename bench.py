@@ -174,6 +174,7 @@ def main():
     ap.add_argument("--max-order", type=int, default=None)
     ap.add_argument("--max-batch", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -286,6 +287,39 @@ def main():
                 "launches": dom_launches,
                 "kernel_ms_total": dom_ms_per * dom_launches, "step_ms_total": t_ms}
 
+    # plain FP64 GPU path, one tuple at a time, vs the mixed batched path on
+    # the same bounded sample (orders 2-4 of the workload)
+    cmp = None
+    if rank == 0 and not args.no_fp64_compare:
+        sample = {k: np.array(ms.sample_tuples(w["exp"], k, 8, 300 + k), dtype=np.int32)
+                  for k in (2, 3, 4)}
+        rates = {}
+        for label, opts in (("fp64_one_tuple", dict(precision=B.MBE_FP64, max_batch=1)),
+                            ("mixed_batched", dict(precision=B.MBE_MIXED_BF16X3,
+                                                   max_batch=args.max_batch))):
+            mm = B.MBE(local, timing=1, **opts)
+            mm.load(h, eri, w["nel"])
+            B.mbe_set_reference(mm.ctx, w["ref"], w["exp"])
+            B.mbe_reset_stats(mm.ctx)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            nt = 0
+            for k, tk in sample.items():
+                B.mbe_solve_tuples(mm.ctx, tk, k)
+                nt += len(tk)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            s2 = B.mbe_get_stats(mm.ctx)
+            rates[label] = {"value": nt / dt, "unit": UNIT, "tuples": nt,
+                            "sigma_tflops_tensor_core": (s2["dom_flops"] / (s2["dom_ms"] * 1e-3)
+                                                         / 1e12) if s2["dom_ms"] else None,
+                            "sigma_tflops_fp64": (s2["fp64_flops"] / (s2["fp64_ms"] * 1e-3) / 1e12)
+                            if s2["fp64_ms"] else None}
+            mm.close()
+        rates["speedup"] = rates["mixed_batched"]["value"] / rates["fp64_one_tuple"]["value"]
+        rates["sample"] = "8 seeded random tuples each of orders 2, 3, 4 of " + args.workload
+        cmp = rates
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         rate, dt, desc, cores = oracle_sample_rate(w, h, eri)
@@ -321,6 +355,7 @@ def main():
                 "davidson_iters_mean": st["iters_total"] / max(st["casci"], 1),
                 "noconv": st["noconv"],
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "mixed_vs_fp64_gpu": cmp,
                 "gpu_launches": int(st["launches"]), "clocks": clk,
                 "total_energy": res["total"]}
         print(json.dumps(line), flush=True)

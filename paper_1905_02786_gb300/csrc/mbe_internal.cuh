@@ -194,6 +194,7 @@ struct BinProblem {
   DevBuf<double> hp;             // B * n * n   (h' = heff - 1/2 sum_r (pr|rq))
   DevBuf<double> gp;             // B * npair * npair
   DevBuf<double> jk;             // B * 2 * n * n  (J_pq = (pp|qq), K_pq = (pq|qp))
+  DevBuf<uint8_t> gsplit;        // g' as bf16 hi/lo in the tensor-core operand layout
 };
 
 // ------------------------------------------------------------ launchers

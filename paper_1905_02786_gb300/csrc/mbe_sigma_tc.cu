@@ -146,15 +146,46 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bflo
   lo = __float2bfloat16_rn(x - __bfloat162float(hi));
 }
 
-// One CTA = tuple b (blockIdx.y) x rows [a0, a0 + R) (blockIdx.x).
-__global__ void __launch_bounds__(TC_THREADS, 1)
-k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad, int R,
-           const double* __restrict__ gp_all, const float* __restrict__ c, int64_t c_stride,
+// Split of g' into bf16 hi + lo in the K-major core-matrix layout of the A
+// operand, once per tuple (the sigma kernel copies it into shared memory):
+// gsplit[b] = {hi[128 x kpad], lo[128 x kpad]}, rows >= npair and K >= npair 0.
+__global__ void k_split_gp(const double* __restrict__ gp_all, int npair, int kpad,
+                           uint8_t* __restrict__ gsplit) {
+  const int b = blockIdx.y;
+  const double* g = gp_all + (int64_t)b * npair * npair;
+  const uint32_t slice = (uint32_t)TC_M * kpad * 2;
+  uint8_t* hi = gsplit + (int64_t)b * 2 * slice;
+  uint8_t* lo = hi + slice;
+  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < TC_M * (kpad >> 3);
+       it += gridDim.x * blockDim.x) {
+    const int row = it / (kpad >> 3), kb = (it % (kpad >> 3)) * 8;
+    __align__(16) __nv_bfloat16 h8[8], l8[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+      const int k = kb + j;
+      const double dv = (row < npair && k < npair) ? g[(int64_t)row * npair + k] : 0.0;
+      const __nv_bfloat16 hh = __double2bfloat16(dv);
+      h8[j] = hh;
+      l8[j] = __double2bfloat16(dv - (double)__bfloat162float(hh));
+    }
+    const uint32_t off = kmajor_offset(row, kb, kpad);
+    *(uint4*)(hi + off) = *(uint4*)h8;
+    *(uint4*)(lo + off) = *(uint4*)l8;
+  }
+}
+
+// One CTA = tuple b (blockIdx.y) x rows [a0, a0 + R) (blockIdx.x); R rows of
+// W = 128 / R column strings form one 128-determinant MMA tile.
+template <int R>
+__global__ void __launch_bounds__(TC_THREADS, 2)
+k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad,
+           const uint8_t* __restrict__ gsplit, const float* __restrict__ c, int64_t c_stride,
            const int32_t* __restrict__ active, float* __restrict__ X, int64_t x_stride,
            int32_t* __restrict__ err) {
+  constexpr int W = TC_N / R;
+  constexpr int WP = W + 1;            // padded row of the column-link table
   const int b = blockIdx.y;
   if (active && !active[b]) return;
-  const int W = TC_N / R;
   const int a0 = blockIdx.x * R;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -167,39 +198,32 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad, int 
   uint8_t* sB_lo = smem + L.b_lo;
   float* sC = (float*)(smem + L.c_rows);
   float* sX = (float*)(smem + L.x_rows);
-  int32_t* sLk = (int32_t*)(smem + L.link_k);     // [P][W + 1]
+  int32_t* sLk = (int32_t*)(smem + L.link_k);     // [P][WP]
   int32_t* sLa = (int32_t*)(smem + L.link_a);     // [r][P]
   const float* cb = c + (int64_t)b * c_stride;
-  const int64_t N = (int64_t)nstr * nstr;
 
-  // ---- setup: g' split into bf16 hi/lo (rows >= npair and K >= npair zero)
-  const double* g = gp_all + (int64_t)b * npair * npair;
-  for (int it = tid; it < TC_M * (kpad >> 3); it += TC_THREADS) {
-    const int row = it / (kpad >> 3), kb = (it % (kpad >> 3)) * 8;
-    __align__(16) __nv_bfloat16 h8[8], l8[8];
-#pragma unroll
-    for (int j = 0; j < 8; j++) {
-      const int k = kb + j;
-      // split the FP64 value: hi from the double, lo from the remainder
-      const double dv = (row < npair && k < npair) ? g[(int64_t)row * npair + k] : 0.0;
-      const __nv_bfloat16 hh = __double2bfloat16(dv);
-      h8[j] = hh;
-      l8[j] = __double2bfloat16(dv - (double)__bfloat162float(hh));
+  // ---- setup: the pre-split g' (contiguous hi, lo) into shared memory
+  {
+    const uint32_t slice = (uint32_t)TC_M * kpad * 2;
+    const uint4* src = (const uint4*)(gsplit + (int64_t)b * 2 * slice);
+    uint4* dhi = (uint4*)sA_hi;
+    uint4* dlo = (uint4*)sA_lo;
+    const int n16 = (int)(slice >> 4);
+    for (int i = tid; i < n16; i += TC_THREADS) {
+      dhi[i] = src[i];
+      dlo[i] = src[n16 + i];
     }
-    const uint32_t off = kmajor_offset(row, kb, kpad);
-    *(uint4*)(sA_hi + off) = *(uint4*)h8;
-    *(uint4*)(sA_lo + off) = *(uint4*)l8;
   }
   for (int it = tid; it < R * nstr; it += TC_THREADS) {
-    const int r = it / nstr, k = it % nstr;
+    const int r = it / nstr, k = it - r * nstr;
     const int a = a0 + r;
-    sC[it] = a < nstr ? cb[(int64_t)a * nstr + k] : 0.f;
+    sC[it] = a < nstr ? cb[a * nstr + k] : 0.f;
     sX[it] = 0.f;
   }
   for (int it = tid; it < R * npair; it += TC_THREADS) {
-    const int r = it / npair, P = it % npair;
+    const int r = it / npair, P = it - r * npair;
     const int a = a0 + r;
-    sLa[it] = a < nstr ? link[(int64_t)a * npair + P] : -1;
+    sLa[it] = a < nstr ? link[a * npair + P] : -1;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -217,44 +241,59 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad, int 
   const uint32_t tmem = tmem_base_sh;
   const uint32_t idesc = make_idesc(TC_M, TC_N);
   const uint32_t sbo = (uint32_t)(kpad >> 3) * 128u;
+  const int nkb = kpad >> 3;
   uint32_t phase = 0;
   bool ok = true;
+
+  // gather mapping: thread -> column n = tid % 128 (fixed), P-blocks
+  // pb = 8 (tid / 128 + 2 i)
+  const int gn = tid & (TC_N - 1);
+  const int gr = gn / W, gj = gn % W;            // W is a power of two
+  const int ga = a0 + gr;
+  const int32_t* la = sLa + gr * npair;
+  const float* crow = sC + gr * nstr;
+  // epilogue mapping: TMEM lanes = pairs P, 64 columns per warp group
+  const int eP = 32 * (warp & 3) + lane;
+  const int ec0 = 64 * (warp >> 2);
 
   for (int k0 = 0; k0 < nstr && ok; k0 += W) {
     // ---- link entries of the column strings of this tile, [P][j]
     for (int it = tid; it < W * npair; it += TC_THREADS) {
-      const int j = it / npair, P = it % npair;
+      const int j = it / npair, P = it - j * npair;
       const int k = k0 + j;
-      sLk[P * (W + 1) + j] = k < nstr ? link[(int64_t)k * npair + P] : -1;
+      sLk[P * WP + j] = k < nstr ? link[k * npair + P] : -1;
     }
     __syncthreads();
-    // ---- gather D (column n = r * W + j <-> determinant (a0 + r, k0 + j))
-    for (int it = tid; it < TC_N * (kpad >> 3); it += TC_THREADS) {
-      const int n = it % TC_N, pb = (it / TC_N) * 8;
-      const int r = n / W, j = n % W;
-      const int a = a0 + r, k = k0 + j;
-      __align__(16) __nv_bfloat16 h8[8], l8[8];
+    // ---- gather D (column n = r W + j <-> determinant (a0 + r, k0 + j))
+    {
+      const int k = k0 + gj;
+      const bool col_ok = ga < nstr && k < nstr;
+      const float* ccol = cb + k;                 // column k of c, row stride nstr
+      for (int kb = tid >> 7; kb < nkb; kb += 2) {
+        const int pb = kb * 8;
+        __align__(16) __nv_bfloat16 h8[8], l8[8];
 #pragma unroll
-      for (int q = 0; q < 8; q++) {
-        const int P = pb + q;
-        float v = 0.f;
-        if (P < npair && a < nstr && k < nstr) {
-          const int32_t ta = sLa[r * npair + P];
-          if (ta >= 0) {
-            float x = cb[(int64_t)(ta >> 1) * nstr + k];
-            v += (ta & 1) ? -x : x;
+        for (int q = 0; q < 8; q++) {
+          const int P = pb + q;
+          float v = 0.f;
+          if (col_ok && P < npair) {
+            const int32_t ta = la[P];
+            if (ta >= 0) {
+              const float x = ccol[(ta >> 1) * nstr];
+              v = (ta & 1) ? -x : x;
+            }
+            const int32_t tk = sLk[P * WP + gj];
+            if (tk >= 0) {
+              const float x = crow[tk >> 1];
+              v += (tk & 1) ? -x : x;
+            }
           }
-          const int32_t tk = sLk[P * (W + 1) + j];
-          if (tk >= 0) {
-            float x = sC[r * nstr + (tk >> 1)];
-            v += (tk & 1) ? -x : x;
-          }
+          split_bf16(v, h8[q], l8[q]);
         }
-        split_bf16(v, h8[q], l8[q]);
+        const uint32_t off = kmajor_offset(gn, pb, kpad);
+        *(uint4*)(sB_hi + off) = *(uint4*)h8;
+        *(uint4*)(sB_lo + off) = *(uint4*)l8;
       }
-      const uint32_t off = kmajor_offset(n, pb, kpad);
-      *(uint4*)(sB_hi + off) = *(uint4*)h8;
-      *(uint4*)(sB_lo + off) = *(uint4*)l8;
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -266,7 +305,7 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad, int 
       const uint32_t bhi = smem_u32(sB_hi), blo = smem_u32(sB_lo);
       uint32_t acc = 0;
       for (int ks = 0; ks < (kpad >> 4); ks++) {
-        const uint32_t koff = (uint32_t)ks * 256u;   // two core matrices along K
+        const uint32_t koff = (uint32_t)ks * 256u;
         mma_bf16(tmem, make_desc(ahi + koff, 128, sbo), make_desc(bhi + koff, 128, sbo), idesc, acc);
         acc = 1;
         mma_bf16(tmem, make_desc(ahi + koff, 128, sbo), make_desc(blo + koff, 128, sbo), idesc, 1);
@@ -275,7 +314,7 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad, int 
       mma_commit(&mbar);
     }
     const int timed_out = mbar_wait(&mbar, phase) ? 0 : 1;
-    if (__syncthreads_or(timed_out)) {   // block-uniform decision
+    if (__syncthreads_or(timed_out)) {
       ok = false;
       if (tid == 0) atomicExch(err, MBE_ECUDA);
     }
@@ -283,18 +322,18 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad, int 
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     // ---- epilogue: E from TMEM, push 1/2 s E into X rows
     if (ok) {
-      const int P = 32 * (warp & 3) + lane;
-      const int col0 = 64 * (warp >> 2);
+      const int32_t* lk = sLk + eP * WP;
+#pragma unroll 1
       for (int cc = 0; cc < 64; cc += 16) {
         float e[16];
-        tmem_ld16(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(col0 + cc), e);
-        if (P < npair) {
+        tmem_ld16(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(ec0 + cc), e);
+        if (eP < npair) {
 #pragma unroll
           for (int q = 0; q < 16; q++) {
-            const int n = col0 + cc + q;
+            const int n = ec0 + cc + q;
             const int r = n / W, j = n % W;
-            if (a0 + r >= nstr || k0 + j >= nstr) continue;
-            const int32_t t = sLk[P * (W + 1) + j];
+            if (a0 + r >= nstr) continue;
+            const int32_t t = lk[j];               // -1 for columns beyond nstr
             if (t >= 0) atomicAdd(&sX[r * nstr + (t >> 1)], (t & 1) ? -0.5f * e[q] : 0.5f * e[q]);
           }
         }
@@ -306,14 +345,13 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad, int 
   }
   // ---- write the X rows
   for (int it = tid; it < R * nstr; it += TC_THREADS) {
-    const int r = it / nstr, k = it % nstr;
+    const int r = it / nstr, k = it - r * nstr;
     const int a = a0 + r;
-    if (a < nstr) X[(int64_t)b * x_stride + (int64_t)a * nstr + k] = sX[it];
+    if (a < nstr) X[(int64_t)b * x_stride + a * nstr + k] = sX[it];
   }
   __syncthreads();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
-  (void)N;
 }
 
 // sigma(a,b) = X(a,b) + X(b,a) + shift (S^2 c)(a,b), FP32 output
@@ -390,9 +428,18 @@ void sigma_tc(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const float* c, int64_
   const int64_t N = bp.ndet;
   if (w.Xf.n < (size_t)bp.B * N) w.Xf.reset(&ctx->pool, (size_t)bp.B * N);
   if (!w.err.ptr) w.err.reset(&ctx->pool, 1);
+  // g' split once per batch (it is constant over the Davidson iteration)
+  const size_t gbytes = (size_t)bp.B * 2 * TC_M * kpad * 2;
+  if (bp.gsplit.n != gbytes) {
+    bp.gsplit.reset(&ctx->pool, gbytes);
+    k_split_gp<<<dim3(8, bp.B), 256, 0, ctx->stream>>>(bp.gp.ptr, npair, kpad, bp.gsplit.ptr);
+    CU_LAUNCH_CHECK();
+  }
   static int attr_done[64] = {0};
   if (!attr_done[ctx->device]) {
-    CU_CHECK(cudaFuncSetAttribute(k_sigma_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CU_CHECK(cudaFuncSetAttribute(k_sigma_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  227 * 1024 - 1024));
+    CU_CHECK(cudaFuncSetAttribute(k_sigma_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   227 * 1024 - 1024));
     attr_done[ctx->device] = 1;
   }
@@ -400,9 +447,14 @@ void sigma_tc(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const float* c, int64_
   dim3 grid((unsigned)((nstr + R - 1) / R), bp.B);
   cudaEvent_t ev;
   ctx->dom_timer.begin(ctx->stream, ctx->opt.timing != 0, &ev);
-  k_sigma_tc<<<grid, TC_THREADS, L.total, ctx->stream>>>(bp.tab->link.ptr, nstr, npair, kpad, R,
-                                                          bp.gp.ptr, c, c_stride, active, w.Xf.ptr,
-                                                          N, w.err.ptr);
+  if (R == 2)
+    k_sigma_tc<2><<<grid, TC_THREADS, L.total, ctx->stream>>>(bp.tab->link.ptr, nstr, npair, kpad,
+                                                               bp.gsplit.ptr, c, c_stride, active,
+                                                               w.Xf.ptr, N, w.err.ptr);
+  else
+    k_sigma_tc<1><<<grid, TC_THREADS, L.total, ctx->stream>>>(bp.tab->link.ptr, nstr, npair, kpad,
+                                                               bp.gsplit.ptr, c, c_stride, active,
+                                                               w.Xf.ptr, N, w.err.ptr);
   CU_LAUNCH_CHECK();
   ctx->dom_timer.end(ctx->stream, ev);
   ctx->stats.dom_launches += 1;
