@@ -87,6 +87,12 @@ typedef struct mbe_options {
                            events (mbe_stats.dom_ms)                         */
   int verbose;          /* 1: print per-iteration Davidson residual summaries
                            to stderr                                         */
+  int backward_share;   /* what mbe_energy_backward sums: 0 the whole
+                           expansion (every CI vector must be held here);
+                           1 only the tuples whose CI vectors this context
+                           holds (tuples sharded over contexts); 2 as 1 plus
+                           the reference-space term (exactly one context of
+                           a sharded run)                                    */
 } mbe_options;
 
 typedef struct mbe_ctx mbe_ctx;
@@ -183,7 +189,11 @@ int mbe_next_tuples(mbe_ctx* ctx, int order, int32_t* tuples_out, int64_t cap,
  * stationary in its CI coefficients, so dE/dh_pq = sum_T c_T gamma^T_pq and
  * dE/d(pq|rs) = 1/2 sum_T c_T Gamma^T_pqrs, with full-space spin-summed RDMs
  * (inactive core included) and c_T = sum_{U in set, U >= T} (-1)^{|U|-|T|}.
- * Needs keep_ci = 1 when the tuples were solved.
+ * Needs keep_ci = 1 when the reference and the tuples were solved.  With
+ * opt.backward_share = 0 a tuple with a non-zero c_T whose CI vector is not
+ * held returns MBE_ESTATE; with 1 or 2 such tuples are skipped (they were
+ * solved by another context) so that the outputs of all contexts sum to the
+ * gradient.
  *  scale  multiplies the outputs (the incoming dL/dE)
  *  dh     norb*norb (symmetric)
  *  deri   npair*npair, gradient w.r.t. the symmetric packed eri matrix

@@ -39,7 +39,8 @@ class mbe_options(ctypes.Structure):
                 ("conv_tol_r", ctypes.c_double), ("conv_tol_e", ctypes.c_double),
                 ("spin_shift", ctypes.c_double), ("keep_ci", ctypes.c_int),
                 ("deterministic", ctypes.c_int), ("mem_cap_bytes", ctypes.c_int64),
-                ("timing", ctypes.c_int), ("verbose", ctypes.c_int)]
+                ("timing", ctypes.c_int), ("verbose", ctypes.c_int),
+                ("backward_share", ctypes.c_int)]
 
 
 _lib = None
@@ -220,6 +221,11 @@ class MBE:
             if callback:
                 callback(rec)
         return dict(eps_ref=e_ref, orders=orders, total=total)
+
+    def backward(self, scale=1.0):
+        """dE/dh (norb x norb) and dE/d eri_packed (npair x npair) of the
+        expansion run last (needs keep_ci=1)."""
+        return mbe_energy_backward(self.ctx, self.norb, scale)
 
 
 class mbe_stats(ctypes.Structure):

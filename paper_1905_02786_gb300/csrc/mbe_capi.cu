@@ -92,6 +92,8 @@ int guarded(mbe_ctx* ctx, F&& f) {
   }
 }
 
+}  // namespace
+
 StringTables* get_tables(mbe_ctx* ctx, int n, int nsig) {
   auto key = std::make_pair(n, nsig);
   auto it = ctx->tables.find(key);
@@ -114,6 +116,8 @@ int count_sig(const mbe_ctx* ctx, const std::vector<int>& act) {
   for (int a : act) s += a < ctx->nocc;
   return s;
 }
+
+namespace {
 
 // Solve the CASCI of every active space in `acts`; binned by (n, nsig).
 void solve_jobs(mbe_ctx* ctx, const std::vector<std::vector<int>>& acts, double* eps,
@@ -209,6 +213,7 @@ void mbe_default_options(mbe_options* o) {
   o->mem_cap_bytes = 0;
   o->timing = 0;
   o->verbose = 0;
+  o->backward_share = 0;
 }
 
 int mbe_create(mbe_ctx** out, int device, const mbe_options* opt) {
@@ -537,8 +542,11 @@ int mbe_next_tuples(mbe_ctx* ctx, int order, int32_t* tuples_out, int64_t cap, i
 
 int mbe_energy_backward(mbe_ctx* ctx, double scale, double* dh, double* deri) {
   return guarded(ctx, [&]() -> int {
-    (void)scale; (void)dh; (void)deri;
-    return fail(ctx, MBE_ESTATE, "energy backward not available in this build");
+    if (!dh || !deri) return fail(ctx, MBE_EINVAL, "null output pointer");
+    if (!ctx->norb) return fail(ctx, MBE_ESTATE, "no integrals loaded");
+    if (ctx->opt.backward_share < 0 || ctx->opt.backward_share > 2)
+      return fail(ctx, MBE_EINVAL, "backward_share must be 0, 1 or 2");
+    return backward_run(ctx, scale, dh, deri);
   });
 }
 

@@ -550,3 +550,14 @@ void s2_apply(mbe_ctx* ctx, BinProblem& bp, const double* c, int64_t c_stride, d
                                    c_stride, active, out, out_stride);
   CU_LAUNCH_CHECK();
 }
+
+void gather_d_fp64(mbe_ctx* ctx, const StringTables* tab, const double* c, double* D) {
+  const int64_t ndet = (int64_t)tab->nstr * tab->nstr;
+  DevBuf<int32_t> bmap(&ctx->pool, 1);
+  CU_CHECK(cudaMemsetAsync(bmap.ptr, 0, sizeof(int32_t), ctx->stream));
+  int64_t blocks = (ndet + 255) / 256;
+  if (blocks > 2048) blocks = 2048;
+  k_gather_fp64<<<dim3((unsigned)blocks, 1), 256, 0, ctx->stream>>>(
+      tab->link.ptr, tab->nstr, tab->npair, c, ndet, nullptr, bmap.ptr, D);
+  CU_LAUNCH_CHECK();
+}

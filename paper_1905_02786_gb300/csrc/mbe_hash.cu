@@ -211,6 +211,35 @@ __global__ void k_gen_write(DevHash h, const int32_t* __restrict__ parents, int 
   }
 }
 
+
+// MBE coefficient of every processed tuple (Moebius inversion of Eq. 3):
+// each tuple T adds (-1)^(|T| - |S|) to the coefficient of every non-empty
+// subtuple S (itself included); the empty subtuple is counted in coef_ref.
+__global__ void k_mbe_coef(DevHash h, const int32_t* __restrict__ tuples, int order, int64_t ntup,
+                           int32_t* __restrict__ coef, int32_t* __restrict__ coef_ref,
+                           int32_t* __restrict__ err) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntup) return;
+  int orb[MBE_MAX_ORDER];
+  for (int i = 0; i < order; i++) orb[i] = tuples[t * order + i];
+  const unsigned full = (1u << order) - 1u;
+  for (unsigned m = 1; m <= full; m++) {
+    unsigned long long k0 = 0, k1 = 0;
+    for (int i = 0; i < order; i++)
+      if ((m >> i) & 1u) {
+        const int o = orb[i];
+        if (o < 64) k0 |= 1ull << o; else k1 |= 1ull << (o - 64);
+      }
+    const int64_t slot = hash_find(h, k0, k1);
+    if (slot < 0) {
+      atomicExch(err, MBE_ELOOKUP);
+      continue;
+    }
+    atomicAdd(&coef[slot], ((order - __popc(m)) & 1) ? -1 : 1);
+  }
+  atomicAdd(coef_ref, (order & 1) ? -1 : 1);
+}
+
 DevHash dev_hash(mbe_ctx* ctx) {
   DevHash h;
   h.keys = ctx->hash.keys.ptr;
@@ -299,4 +328,12 @@ int64_t next_tuples_device(mbe_ctx* ctx, const int32_t* parents_dev, int order_p
                                                             exp_dev, nexp, off.ptr, out.ptr);
   CU_LAUNCH_CHECK();
   return total;
+}
+
+void mbe_coef_launch(mbe_ctx* ctx, const int32_t* tuples_dev, int order, int64_t ntup,
+                     int32_t* coef_dev, int32_t* coef_ref_dev, int32_t* err_dev) {
+  if (ntup == 0) return;
+  k_mbe_coef<<<(unsigned)((ntup + 127) / 128), 128, 0, ctx->stream>>>(
+      dev_hash(ctx), tuples_dev, order, ntup, coef_dev, coef_ref_dev, err_dev);
+  CU_LAUNCH_CHECK();
 }

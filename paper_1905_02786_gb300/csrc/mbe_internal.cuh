@@ -199,6 +199,12 @@ struct BinProblem {
 
 // ------------------------------------------------------------ launchers
 void build_string_tables(mbe_ctx* ctx, StringTables* t);
+StringTables* get_tables(mbe_ctx* ctx, int n, int nsig);
+int count_sig(const mbe_ctx* ctx, const std::vector<int>& act);
+// D[P][K] = (E+_P c)(K) for one CI vector c (ndet) and every packed pair P
+void gather_d_fp64(mbe_ctx* ctx, const StringTables* tab, const double* c, double* D);
+// energy gradient of the processed expansion (mbe_energy_backward)
+int backward_run(mbe_ctx* ctx, double scale, double* dh_host, double* deri_host);
 void launch_effints(mbe_ctx* ctx, BinProblem& bp);
 void launch_hdiag(mbe_ctx* ctx, BinProblem& bp, double spin_shift, double* hd);
 
@@ -243,6 +249,10 @@ void increments_kernel_launch(mbe_ctx* ctx, const int32_t* tuples_dev, int order
                               double thr, double* inc_dev, uint8_t* keep_dev,
                               int32_t* err_dev);
 double kahan_sum_device(mbe_ctx* ctx, const double* v, int64_t n);
+// adds the MBE coefficient contributions of one order's tuples to coef (per
+// hash slot) and coef_ref (the empty tuple)
+void mbe_coef_launch(mbe_ctx* ctx, const int32_t* tuples_dev, int order, int64_t ntup,
+                     int32_t* coef_dev, int32_t* coef_ref_dev, int32_t* err_dev);
 int64_t next_tuples_device(mbe_ctx* ctx, const int32_t* parents_dev, int order_prev,
                            int64_t nparents, const int32_t* exp_dev, int nexp,
                            DevBuf<int32_t>& out);

@@ -46,21 +46,38 @@ def torch_allgather(group=None):
     return gather
 
 
+def torch_allreduce_sum(group=None):
+    """sum of float64 arrays over torch.distributed (same shape on all ranks)."""
+    import torch
+    import torch.distributed as dist
+
+    def reduce(a: np.ndarray) -> np.ndarray:
+        dev = torch.device("cuda", torch.cuda.current_device()) \
+            if dist.get_backend(group) == "nccl" else torch.device("cpu")
+        t = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(dev)
+        dist.all_reduce(t, group=group)
+        return t.cpu().numpy()
+    return reduce
+
+
 def run_expansion(ctx, ref, exp, max_order, thr=0.0, rank=0, world=1, allgather=None,
-                  solve=None, callback=None):
+                  solve=None, callback=None, api=None):
     """Run orders 1..max_order; returns dict(eps_ref, orders, total, ntup).
 
-    ``solve(ctx, tuples, k) -> eps`` defaults to mbe_solve_tuples; tests may
-    pass a host solver to exercise the sharding logic without a GPU."""
+    ``api`` is the module of C-ABI wrappers (default: the binding);
+    ``solve(ctx, tuples, k) -> eps`` defaults to its mbe_solve_tuples.  Tests
+    pass a host stand-in for both to exercise the sharding logic without a
+    GPU."""
+    B_ = api or B
     if solve is None:
         def solve(c, t, k):
-            return B.mbe_solve_tuples(c, t, k)[0]
-    e_ref = B.mbe_set_reference(ctx, ref, exp)
+            return B_.mbe_solve_tuples(c, t, k)[0]
+    e_ref = B_.mbe_set_reference(ctx, ref, exp)
     orders = []
     total = e_ref
     ntot = 0
     for k in range(1, max_order + 1):
-        tuples = B.mbe_next_tuples(ctx, k)
+        tuples = B_.mbe_next_tuples(ctx, k)
         n = len(tuples)
         if n == 0:
             break
@@ -69,13 +86,25 @@ def run_expansion(ctx, ref, exp, max_order, thr=0.0, rank=0, world=1, allgather=
         if world > 1:
             counts = [len(shard_indices(n, r, world)) for r in range(world)]
             eps = merge_shards(allgather(np.asarray(eps_local, dtype=np.float64), counts), n, world)
-            B.mbe_set_order_energies(ctx, tuples, eps, k)
+            B_.mbe_set_order_energies(ctx, tuples, eps, k)
         else:
             eps = eps_local
-        inc, keep, e_order, total = B.mbe_increments(ctx, k, thr, n)
+        inc, keep, e_order, total = B_.mbe_increments(ctx, k, thr, n)
         ntot += n
         rec = dict(order=k, tuples=tuples, eps=eps, inc=inc, keep=keep, E_order=e_order)
         orders.append(rec)
         if callback:
             callback(rec)
     return dict(eps_ref=e_ref, orders=orders, total=total, ntup=ntot)
+
+
+def sharded_backward(ctx, norb, rank=0, world=1, allreduce=None, api=None):
+    """Gradient of a sharded expansion: each context sums the RDMs of the CI
+    vectors it holds (created with backward_share = 2 on rank 0 and 1 on the
+    others, so the reference term is counted once) and the shares are summed
+    over the ranks."""
+    B_ = api or B
+    dh, deri = B_.mbe_energy_backward(ctx, norb)
+    if world > 1:
+        dh, deri = allreduce(dh), allreduce(deri)
+    return dh, deri
