@@ -169,3 +169,46 @@ def test_autograd_function(lib):
     assert abs(e.item() - om.run_mbe(h, eri, nocc, ref, exp, 3, 0.0)["total"]) < 1e-10
     assert np.max(np.abs(ht.grad.numpy() - 2.0 * odh)) < 2 * TOL
     assert np.max(np.abs(et.grad.numpy() - 2.0 * odg)) < 2 * TOL
+
+
+def test_grad_workload_fd_sample(lib):
+    """8e/20o, CAS(4e,4o) reference over orbitals 2-5, unscreened to order 4
+    (2,516 tuples): central differences (step 1e-5) of the GPU energy on a
+    seeded sample of unique integrals, and the trace invariant
+    tr dE/dh = N_el (the MBE coefficients sum to one)."""
+    w = ms.workload("grad_8e20o")
+    h, eri, _ = ms.workload_integrals("grad_8e20o")
+    nocc, n = w["nocc"], w["norb"]
+    _, dh, dg = gpu_grad(lib, h, eri, nocc, w["ref"], w["exp"], w["max_order"], 0.0)
+    assert abs(np.trace(dh) - w["nel"]) < 1e-9
+
+    def energy(h_, e_):
+        m = lib.MBE(0)
+        m.load(h_, e_, w["nel"])
+        e = m.run(w["ref"], w["exp"], w["max_order"], 0.0)["total"]
+        m.close()
+        return e
+
+    rng = np.random.default_rng(3)
+    step = 1e-5
+    for _ in range(3):
+        p, q = sorted(rng.integers(0, n, 2))
+        hp, hm = h.copy(), h.copy()
+        for M, s in ((hp, step), (hm, -step)):
+            M[p, q] += s
+            if p != q:
+                M[q, p] += s
+        fd = (energy(hp, eri) - energy(hm, eri)) / (2 * step)
+        an = dh[p, q] * (1 if p == q else 2)
+        assert abs(fd - an) <= 1e-6 * abs(an) + 1e-8, (p, q, fd, an)
+    P = ms.npair(n)
+    for _ in range(3):
+        a, b = sorted(rng.integers(0, P, 2))
+        ep, em = eri.copy(), eri.copy()
+        for M, s in ((ep, step), (em, -step)):
+            M[a, b] += s
+            if a != b:
+                M[b, a] += s
+        fd = (energy(h, ep) - energy(h, em)) / (2 * step)
+        an = dg[a, b] * (1 if a == b else 2)
+        assert abs(fd - an) <= 1e-6 * abs(an) + 1e-8, (a, b, fd, an)
