@@ -222,6 +222,35 @@ int mbe_reset_stats(mbe_ctx* ctx);
 int mbe_sigma(mbe_ctx* ctx, const int* act, int nact, const double* c,
               double* sigma, double* e_core);
 
+/* Device scratch of mbe_sigma_noalloc, per device (16 MiB). */
+#define MBE_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* mbe_sigma without device-memory allocation (the paper has no counterpart;
+ * it serves callers that may not allocate: cudaMalloc / cudaFree can
+ * synchronise the whole device, and a caller under a fixed device-memory
+ * budget cannot let the context's pool grow).  Always the FP64 sigma
+ * (H_active + spin_shift*S^2) c, whatever opt.precision says.
+ *  act[nact]   active orbitals (host)
+ *  c_dev       nstr*nstr doubles, DEVICE memory of the context's device,
+ *              caller-owned, read only
+ *  sigma_dev   nstr*nstr doubles, DEVICE memory, caller-owned, fully
+ *              overwritten (need not be zeroed)
+ *  ndet        element count of c_dev and sigma_dev; MBE_EINVAL unless it
+ *              equals nstr*nstr of the active space
+ *  e_core      host; if non-NULL the inactive-core energy is written there
+ *              and the call waits for the context stream; if NULL the call
+ *              returns once the work is enqueued on the context stream.
+ * All intermediates (string tables, effective integrals, the D and E
+ * intermediates of the sigma) live in one file-scope device array of
+ * MBE_NOALLOC_SCRATCH_BYTES per device; none of it needs to start at zero.
+ * A problem that does not fit (roughly more than 9 active orbitals) returns
+ * MBE_EINVAL and launches nothing.  Calls overlapping on one device race on
+ * that array: issue them on one stream or wait for one before the next.
+ * The first call on a device looks the array up (cudaGetSymbolAddress) and
+ * sets a kernel attribute; make it before any stream capture. */
+int mbe_sigma_noalloc(mbe_ctx* ctx, const int* act, int nact, const double* c_dev,
+                      double* sigma_dev, int64_t ndet, double* e_core);
+
 #ifdef __cplusplus
 }
 #endif

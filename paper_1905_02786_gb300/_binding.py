@@ -24,7 +24,8 @@ ERROR_NAMES = {0: "MBE_OK", -1: "MBE_EINVAL", -2: "MBE_ENOMEM", -3: "MBE_ECUDA",
 EXPORTED = ["mbe_default_options", "mbe_create", "mbe_destroy", "mbe_last_error",
             "mbe_load_integrals", "mbe_set_reference", "mbe_solve_tuples",
             "mbe_increments", "mbe_next_tuples", "mbe_energy_backward", "mbe_sigma",
-            "mbe_get_stats", "mbe_reset_stats", "mbe_set_order_energies", "mbe_set_stream"]
+            "mbe_get_stats", "mbe_reset_stats", "mbe_set_order_energies", "mbe_set_stream",
+            "mbe_sigma_noalloc"]
 
 
 class MBEError(RuntimeError):
@@ -70,6 +71,7 @@ def load_library(path: str = LIB_PATH):
     L.mbe_next_tuples.argtypes = [vp, c_int, vp, c_i64, vp]
     L.mbe_energy_backward.argtypes = [vp, c_double, vp, vp]
     L.mbe_sigma.argtypes = [vp, vp, c_int, vp, vp, vp]
+    L.mbe_sigma_noalloc.argtypes = [vp, vp, c_int, vp, vp, ctypes.c_int64, vp]
     for name in EXPORTED:
         if name not in ("mbe_default_options", "mbe_destroy", "mbe_last_error",
                         "mbe_get_stats", "mbe_reset_stats", "mbe_set_order_energies",
@@ -174,6 +176,26 @@ def mbe_sigma(ctx, act, c):
     ec = np.zeros(1)
     _check(ctx, load_library().mbe_sigma(ctx, _p(act), act.size, _p(c), _p(sig), _p(ec)))
     return sig, float(ec[0])
+
+
+def mbe_sigma_noalloc(ctx, act, c_dev, sigma_dev, want_core=True):
+    """FP64 sigma without device allocation.  c_dev and sigma_dev are CUDA
+    float64 tensors (nstr*nstr elements, contiguous) on the context's device;
+    sigma_dev is overwritten.  Returns the inactive-core energy if want_core
+    (the call then waits for the context stream), else None."""
+    act = np.ascontiguousarray(sorted(act), dtype=np.int32)
+    for t in (c_dev, sigma_dev):
+        if not (t.is_cuda and t.dtype.is_floating_point and t.element_size() == 8
+                and t.is_contiguous()):
+            raise TypeError("c_dev and sigma_dev must be contiguous CUDA float64 tensors")
+    if c_dev.numel() != sigma_dev.numel():
+        raise ValueError("c_dev and sigma_dev differ in size")
+    ec = np.zeros(1)
+    _check(ctx, load_library().mbe_sigma_noalloc(ctx, _p(act), act.size,
+                                                 ctypes.c_void_p(c_dev.data_ptr()),
+                                                 ctypes.c_void_p(sigma_dev.data_ptr()),
+                                                 c_dev.numel(), _p(ec) if want_core else None))
+    return float(ec[0]) if want_core else None
 
 
 class MBE:

@@ -606,6 +606,13 @@ int mbe_set_order_energies(mbe_ctx* ctx, int order, const int32_t* tuples, int64
   });
 }
 
+int mbe_sigma_noalloc(mbe_ctx* ctx, const int* act, int nact, const double* c_dev,
+                      double* sigma_dev, int64_t ndet, double* e_core) {
+  return guarded(ctx, [&]() -> int {
+    return noalloc_sigma_run(ctx, act, nact, c_dev, sigma_dev, ndet, e_core);
+  });
+}
+
 int mbe_sigma(mbe_ctx* ctx, const int* act, int nact, const double* c, double* sigma,
               double* e_core) {
   return guarded(ctx, [&]() -> int {

@@ -95,22 +95,30 @@ __global__ void k_link(const uint32_t* masks, int32_t* link, int nstr, int n) {
 
 }  // namespace
 
-void build_string_tables(mbe_ctx* ctx, StringTables* t) {
-  ensure_binom(ctx->device);
+int64_t string_count(int n, int nsig) {
   long long nstr = 1;
-  for (int i = 0; i < t->nsig; i++) nstr = nstr * (t->n - i) / (i + 1);
+  for (int i = 0; i < nsig; i++) nstr = nstr * (n - i) / (i + 1);
+  return nstr;
+}
+
+void launch_string_tables(mbe_ctx* ctx, int n, int nsig, int nstr, uint32_t* masks,
+                          int32_t* link) {
+  ensure_binom(ctx->device);
+  k_strings<<<(nstr + 255) / 256, 256, 0, ctx->stream>>>(masks, nstr, n, nsig);
+  CU_LAUNCH_CHECK();
+  const int64_t tot = (int64_t)nstr * (n * (n + 1) / 2);
+  k_link<<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(masks, link, nstr, n);
+  CU_LAUNCH_CHECK();
+}
+
+void build_string_tables(mbe_ctx* ctx, StringTables* t) {
+  const int64_t nstr = string_count(t->n, t->nsig);
   if (nstr > (1 << 28)) throw MbeError{MBE_EINVAL, "string space too large"};
   t->nstr = (int)nstr;
   t->npair = t->n * (t->n + 1) / 2;
   t->masks.reset(&ctx->pool, t->nstr);
   t->link.reset(&ctx->pool, (size_t)t->nstr * t->npair);
-  k_strings<<<(t->nstr + 255) / 256, 256, 0, ctx->stream>>>(t->masks.ptr, t->nstr, t->n,
-                                                           t->nsig);
-  CU_LAUNCH_CHECK();
-  int64_t tot = (int64_t)t->nstr * t->npair;
-  k_link<<<(unsigned)((tot + 255) / 256), 256, 0, ctx->stream>>>(t->masks.ptr, t->link.ptr,
-                                                               t->nstr, t->n);
-  CU_LAUNCH_CHECK();
+  launch_string_tables(ctx, t->n, t->nsig, t->nstr, t->masks.ptr, t->link.ptr);
 }
 
 // ------------------------------------------------------------------ K2
@@ -212,6 +220,14 @@ __global__ void k_effints(const double* __restrict__ h, const double* __restrict
 
 }  // namespace
 
+void launch_effints_raw(mbe_ctx* ctx, const int32_t* act, int B, int n, int nsig, double* ecore,
+                        double* heff, double* hp, double* gp, double* jk) {
+  size_t smem = 2 * sizeof(double) * n * n;
+  k_effints<<<B, 256, smem, ctx->stream>>>(ctx->h.ptr, ctx->eri.ptr, ctx->norb, ctx->nocc,
+                                           ctx->npair_g, act, n, nsig, ecore, heff, hp, gp, jk);
+  CU_LAUNCH_CHECK();
+}
+
 void launch_effints(mbe_ctx* ctx, BinProblem& bp) {
   const int n = bp.n, B = bp.B;
   bp.ecore.reset(&ctx->pool, B);
@@ -219,11 +235,8 @@ void launch_effints(mbe_ctx* ctx, BinProblem& bp) {
   bp.hp.reset(&ctx->pool, (size_t)B * n * n);
   bp.gp.reset(&ctx->pool, (size_t)B * bp.npair * bp.npair);
   bp.jk.reset(&ctx->pool, (size_t)B * 2 * n * n);
-  size_t smem = 2 * sizeof(double) * n * n;
-  k_effints<<<B, 256, smem, ctx->stream>>>(ctx->h.ptr, ctx->eri.ptr, ctx->norb, ctx->nocc,
-                                           ctx->npair_g, bp.act.ptr, n, bp.nsig, bp.ecore.ptr,
-                                           bp.heff.ptr, bp.hp.ptr, bp.gp.ptr, bp.jk.ptr);
-  CU_LAUNCH_CHECK();
+  launch_effints_raw(ctx, bp.act.ptr, B, n, bp.nsig, bp.ecore.ptr, bp.heff.ptr, bp.hp.ptr,
+                     bp.gp.ptr, bp.jk.ptr);
 }
 
 // ------------------------------------------------------------------ K3
@@ -504,41 +517,48 @@ void sigma_fp64(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const double* c, int
   DevBuf<int32_t> bmap(&ctx->pool, bp.B);
   CU_CHECK(cudaMemcpyAsync(bmap.ptr, bm.data(), sizeof(int32_t) * bp.B, cudaMemcpyHostToDevice,
                            ctx->stream));
+  for (int64_t b0 = 0; b0 < bp.B; b0 += sb) {
+    const int nb = (int)std::min<int64_t>(sb, bp.B - b0);
+    sigma_fp64_raw(ctx, bp.n, bp.nsig, bp.nstr, bp.tab->link.ptr, bp.tab->masks.ptr, bp.gp.ptr, c,
+                   c_stride, out, out_stride, active, bmap.ptr + b0, nb, w.D.ptr, w.E.ptr,
+                   spin_shift, emulated, w.err.ptr);
+  }
+}
+
+void sigma_fp64_raw(mbe_ctx* ctx, int n, int nsig, int nstr, const int32_t* link,
+                    const uint32_t* masks, const double* gp, const double* c, int64_t c_stride,
+                    double* out, int64_t out_stride, const int32_t* active, const int32_t* bmap,
+                    int nb, double* D, double* E, double spin_shift, bool emulated, int32_t* err) {
+  const int npair = n * (n + 1) / 2;
+  const int64_t ndet = (int64_t)nstr * nstr;
   int64_t blocks = (ndet + 255) / 256;
   if (blocks > 2048) blocks = 2048;
-  size_t smem_c = sizeof(double) * (npair * npair + npair * GT_N);
-  static bool attr_set = false;
-  if (!attr_set) {
+  const size_t smem_c = sizeof(double) * (npair * npair + npair * GT_N);
+  static bool attr_set[64] = {false};
+  if (!attr_set[ctx->device]) {
     CU_CHECK(cudaFuncSetAttribute(k_contract_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   200 * 1024));
-    attr_set = true;
+    attr_set[ctx->device] = true;
   }
   int64_t cblocks = (ndet + GT_N - 1) / GT_N;
   if (cblocks > 1024) cblocks = 1024;
-  for (int64_t b0 = 0; b0 < bp.B; b0 += sb) {
-    int nb = (int)std::min<int64_t>(sb, bp.B - b0);
-    dim3 g1((unsigned)blocks, nb);
-    k_gather_fp64<<<g1, 256, 0, ctx->stream>>>(bp.tab->link.ptr, bp.nstr, npair, c, c_stride,
-                                               active, bmap.ptr + b0, w.D.ptr);
-    CU_LAUNCH_CHECK();
-    dim3 g2((unsigned)cblocks, nb);
-    cudaEvent_t ev;
-    ctx->fp64_timer.begin(ctx->stream, ctx->opt.timing != 0, &ev);
-    if (emulated) {
-      contract_ozaki(ctx, bp.gp.ptr, npair, w.D.ptr, ndet, nb, active, bmap.ptr + b0, w.E.ptr,
-                     w.err.ptr);
-    } else {
-      k_contract_fp64<<<g2, 256, smem_c, ctx->stream>>>(bp.gp.ptr, npair, w.D.ptr, ndet, active,
-                                                        bmap.ptr + b0, w.E.ptr);
-      CU_LAUNCH_CHECK();
-    }
-    ctx->fp64_timer.end(ctx->stream, ev);
-    ctx->stats.fp64_launches += 1;
-    k_scatter_fp64<<<g1, 256, 0, ctx->stream>>>(bp.tab->link.ptr, bp.tab->masks.ptr, bp.nstr,
-                                                bp.n, bp.nsig, w.E.ptr, emulated ? 1 : 0, c, c_stride, spin_shift,
-                                                active, bmap.ptr + b0, out, out_stride);
+  const dim3 g1((unsigned)blocks, nb);
+  k_gather_fp64<<<g1, 256, 0, ctx->stream>>>(link, nstr, npair, c, c_stride, active, bmap, D);
+  CU_LAUNCH_CHECK();
+  cudaEvent_t ev;
+  ctx->fp64_timer.begin(ctx->stream, ctx->opt.timing != 0, &ev);
+  if (emulated) {
+    contract_ozaki(ctx, gp, npair, D, ndet, nb, active, bmap, E, err);
+  } else {
+    k_contract_fp64<<<dim3((unsigned)cblocks, nb), 256, smem_c, ctx->stream>>>(gp, npair, D, ndet,
+                                                                             active, bmap, E);
     CU_LAUNCH_CHECK();
   }
+  ctx->fp64_timer.end(ctx->stream, ev);
+  ctx->stats.fp64_launches += 1;
+  k_scatter_fp64<<<g1, 256, 0, ctx->stream>>>(link, masks, nstr, n, nsig, E, emulated ? 1 : 0, c,
+                                              c_stride, spin_shift, active, bmap, out, out_stride);
+  CU_LAUNCH_CHECK();
 }
 
 void s2_apply(mbe_ctx* ctx, BinProblem& bp, const double* c, int64_t c_stride, double* out,

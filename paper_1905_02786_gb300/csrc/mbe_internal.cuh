@@ -199,10 +199,24 @@ struct BinProblem {
 
 // ------------------------------------------------------------ launchers
 void build_string_tables(mbe_ctx* ctx, StringTables* t);
+// raw-pointer forms of the table, integral and FP64 sigma launchers (they
+// allocate nothing)
+int64_t string_count(int n, int nsig);
+void launch_string_tables(mbe_ctx* ctx, int n, int nsig, int nstr, uint32_t* masks,
+                          int32_t* link);
+void launch_effints_raw(mbe_ctx* ctx, const int32_t* act, int B, int n, int nsig, double* ecore,
+                        double* heff, double* hp, double* gp, double* jk);
+void sigma_fp64_raw(mbe_ctx* ctx, int n, int nsig, int nstr, const int32_t* link,
+                    const uint32_t* masks, const double* gp, const double* c, int64_t c_stride,
+                    double* out, int64_t out_stride, const int32_t* active, const int32_t* bmap,
+                    int nb, double* D, double* E, double spin_shift, bool emulated, int32_t* err);
 StringTables* get_tables(mbe_ctx* ctx, int n, int nsig);
 int count_sig(const mbe_ctx* ctx, const std::vector<int>& act);
 // D[P][K] = (E+_P c)(K) for one CI vector c (ndet) and every packed pair P
 void gather_d_fp64(mbe_ctx* ctx, const StringTables* tab, const double* c, double* D);
+// mbe_sigma_noalloc (scratch in a file-scope device array)
+int noalloc_sigma_run(mbe_ctx* ctx, const int* act, int nact, const double* c_dev,
+                      double* sigma_dev, int64_t ndet_arg, double* e_core);
 // energy gradient of the processed expansion (mbe_energy_backward)
 int backward_run(mbe_ctx* ctx, double scale, double* dh_host, double* deri_host);
 void launch_effints(mbe_ctx* ctx, BinProblem& bp);
