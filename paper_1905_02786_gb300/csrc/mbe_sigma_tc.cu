@@ -9,18 +9,21 @@
 //   X(a, b) = 1/2 sum_P sum_k <b|E+_P|k> E_P(a, k)        (beta strings)
 // Each CTA owns R full rows a of X (kept in shared memory, no global
 // atomics) and walks the column strings k in tiles; for a tile of
-// N = 128 determinants (a, k) it
+// M = 128 determinants (a, k) it
 //   1. gathers D_P(a,k) = s_a c(J_a,k) + s_k c(a,J_k) for all pairs P
 //      (rows J_a of c read coalesced from global memory, row a of c staged in
-//      shared memory) and splits it into bf16 hi + lo (K-major core-matrix
-//      layout, 16-byte vector stores),
-//   2. one elected thread issues g'_hi D_hi + g'_hi D_lo + g'_lo D_hi as
-//      tcgen05.mma (M = 128 pair rows, N = 128, K = 16 per instruction)
-//      into a 128 x 128 FP32 accumulator in TMEM and commits to an mbarrier,
-//   3. the 8 warps read E back with tcgen05.ld (warp w: TMEM lanes
-//      32 (w mod 4) .. + 31 = pairs P, columns 64 (w / 4) .. + 63) and push
-//      1/2 s E_P(a,k) into X(a, J) for the string J linked to k by P
-//      (shared-memory atomics).
+//      shared memory, the link rows of the tile's column strings staged as
+//      int16) and splits it into bf16 hi + lo as the A operand (one
+//      determinant per row, K = pairs, K-major core-matrix layout, 16-byte
+//      vector stores),
+//   2. one elected thread issues D_hi g'_hi + D_lo g'_hi + D_hi g'_lo as
+//      tcgen05.mma (M = 128 determinants, N = kpad pairs, K = 16 per
+//      instruction; g' is symmetric, so this is E^T) into an FP32
+//      accumulator in TMEM and commits to an mbarrier,
+//   3. every warp reads E^T back with tcgen05.ld (warp w: TMEM lanes
+//      32 (w mod 4) .. + 31 = determinants, every other 8-column chunk of
+//      pairs) and pushes 1/2 s E_P(a,k) into X(a, J) for the string J linked
+//      to k by P (shared-memory atomics); all eight warps carry equal work.
 // Precision: both operands carry ~16 significant bits after the hi/lo split,
 // the dropped lo*lo term and the FP32 accumulation give sigma to ~1e-4 of
 // its largest element; the Davidson iteration corrects this with FP64-grade
@@ -34,8 +37,7 @@ namespace {
 
 constexpr int TC_THREADS = 256;
 constexpr int TC_N = 128;        // determinants per MMA tile (R rows x W cols)
-constexpr int TC_M = 128;        // pair rows of the accumulator (npair <= 120 padded)
-constexpr uint32_t TMEM_COLS = 128;
+constexpr int TC_M = 128;        // MMA M (= TC_N determinants); npair <= 128
 constexpr long long SPIN_LIMIT = 1LL << 28;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -116,10 +118,25 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; i++) v[i] = __uint_as_float(r[i]);
+}
+
 struct TcShared {
   // byte offsets into dynamic shared memory
-  uint32_t a_hi, a_lo, b_hi, b_lo, c_rows, x_rows, link_k, link_a, total;
+  uint32_t d_hi, d_lo, g_hi, g_lo, c_rows, x_rows, link_k, link_a, total;
 };
+
+// odd row stride (in int16) of the staged link rows: conflict-free columns
+__host__ __device__ inline int link_stride(int npair) { return npair | 1; }
 
 __host__ __device__ inline TcShared tc_layout(int kpad, int R, int nstr, int npair, int W) {
   TcShared s;
@@ -129,16 +146,22 @@ __host__ __device__ inline TcShared tc_layout(int kpad, int R, int nstr, int npa
     o += (bytes + 127u) & ~127u;
     return r;
   };
-  s.a_hi = take((uint32_t)TC_M * kpad * 2);
-  s.a_lo = take((uint32_t)TC_M * kpad * 2);
-  s.b_hi = take((uint32_t)TC_N * kpad * 2);
-  s.b_lo = take((uint32_t)TC_N * kpad * 2);
+  s.d_hi = take((uint32_t)TC_M * kpad * 2);
+  s.d_lo = take((uint32_t)TC_M * kpad * 2);
+  s.g_hi = take((uint32_t)kpad * kpad * 2);
+  s.g_lo = take((uint32_t)kpad * kpad * 2);
   s.c_rows = take((uint32_t)R * nstr * 4);
   s.x_rows = take((uint32_t)R * nstr * 4);
-  s.link_k = take((uint32_t)npair * (W + 1) * 4);
+  s.link_k = take((uint32_t)W * link_stride(npair) * 2);
   s.link_a = take((uint32_t)R * npair * 4);
   s.total = o;
   return s;
+}
+
+__host__ __device__ inline uint32_t tmem_cols_for(int kpad) {
+  uint32_t c = 32;
+  while (c < (uint32_t)kpad) c <<= 1;
+  return c;
 }
 
 __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
@@ -146,8 +169,8 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bflo
   lo = __float2bfloat16_rn(x - __bfloat162float(hi));
 }
 
-// Split of g' into bf16 hi + lo in the K-major core-matrix layout of the A
-// operand, once per tuple (the sigma kernel copies it into shared memory):
+// Split of g' into bf16 hi + lo in the K-major core-matrix layout, once per
+// tuple (the sigma kernel copies its first kpad rows into shared memory):
 // gsplit[b] = {hi[128 x kpad], lo[128 x kpad]}, rows >= npair and K >= npair 0.
 __global__ void k_split_gp(const double* __restrict__ gp_all, int npair, int kpad,
                            uint8_t* __restrict__ gsplit) {
@@ -174,8 +197,10 @@ __global__ void k_split_gp(const double* __restrict__ gp_all, int npair, int kpa
   }
 }
 
-// One CTA = tuple b (blockIdx.y) x rows [a0, a0 + R) (blockIdx.x); R rows of
-// W = 128 / R column strings form one 128-determinant MMA tile.
+// One CTA = tuple b (blockIdx.y) x rows [a0, a0 + R) of X (blockIdx.x).  An
+// MMA tile is M = 128 determinants m = r W + j <-> (a0 + r, k0 + j), r < R,
+// j < W = 128 / R; the accumulator holds E^T (lane m, column P), computed
+// as D^T g' (g' is symmetric) with N = kpad pair columns.
 template <int R>
 __global__ void __launch_bounds__(TC_THREADS, 2)
 k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad,
@@ -183,7 +208,7 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad,
            const int32_t* __restrict__ active, float* __restrict__ X, int64_t x_stride,
            int32_t* __restrict__ err) {
   constexpr int W = TC_N / R;
-  constexpr int WP = W + 1;            // padded row of the column-link table
+  const int LS = link_stride(npair);
   const int b = blockIdx.y;
   if (active && !active[b]) return;
   const int a0 = blockIdx.x * R;
@@ -192,24 +217,25 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad,
   __shared__ uint64_t mbar;
   __shared__ uint32_t tmem_base_sh;
   const TcShared L = tc_layout(kpad, R, nstr, npair, W);
-  uint8_t* sA_hi = smem + L.a_hi;
-  uint8_t* sA_lo = smem + L.a_lo;
-  uint8_t* sB_hi = smem + L.b_hi;
-  uint8_t* sB_lo = smem + L.b_lo;
+  uint8_t* sD_hi = smem + L.d_hi;
+  uint8_t* sD_lo = smem + L.d_lo;
+  uint8_t* sG_hi = smem + L.g_hi;
+  uint8_t* sG_lo = smem + L.g_lo;
   float* sC = (float*)(smem + L.c_rows);
   float* sX = (float*)(smem + L.x_rows);
-  int32_t* sLk = (int32_t*)(smem + L.link_k);     // [P][WP]
+  int16_t* sLk = (int16_t*)(smem + L.link_k);     // [j][LS]
   int32_t* sLa = (int32_t*)(smem + L.link_a);     // [r][P]
   const float* cb = c + (int64_t)b * c_stride;
+  const uint32_t tcols = tmem_cols_for(kpad);
 
-  // ---- setup: the pre-split g' (contiguous hi, lo) into shared memory
+  // ---- setup: the first kpad rows of the pre-split g' into shared memory
   {
     const uint32_t slice = (uint32_t)TC_M * kpad * 2;
     const uint4* src = (const uint4*)(gsplit + (int64_t)b * 2 * slice);
-    uint4* dhi = (uint4*)sA_hi;
-    uint4* dlo = (uint4*)sA_lo;
-    const int n16 = (int)(slice >> 4);
-    for (int i = tid; i < n16; i += TC_THREADS) {
+    uint4* dhi = (uint4*)sG_hi;
+    uint4* dlo = (uint4*)sG_lo;
+    const int n16 = (int)(slice >> 4), m16 = (kpad * kpad * 2) >> 4;
+    for (int i = tid; i < m16; i += TC_THREADS) {
       dhi[i] = src[i];
       dlo[i] = src[n16 + i];
     }
@@ -228,7 +254,7 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad,
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_base_sh)),
-                 "r"(TMEM_COLS));
+                 "r"(tcols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
@@ -239,32 +265,36 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad,
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base_sh;
-  const uint32_t idesc = make_idesc(TC_M, TC_N);
+  const uint32_t idesc = make_idesc(TC_M, kpad);
   const uint32_t sbo = (uint32_t)(kpad >> 3) * 128u;
   const int nkb = kpad >> 3;
   uint32_t phase = 0;
   bool ok = true;
 
-  // gather mapping: thread -> column n = tid % 128 (fixed), P-blocks
+  // gather mapping: thread -> determinant m = tid % 128 (fixed), P-blocks
   // pb = 8 (tid / 128 + 2 i)
-  const int gn = tid & (TC_N - 1);
-  const int gr = gn / W, gj = gn % W;            // W is a power of two
+  const int gm = tid & (TC_M - 1);
+  const int gr = gm / W, gj = gm % W;            // W is a power of two
   const int ga = a0 + gr;
   const int32_t* la = sLa + gr * npair;
   const float* crow = sC + gr * nstr;
-  // epilogue mapping: TMEM lanes = pairs P, 64 columns per warp group
-  const int eP = 32 * (warp & 3) + lane;
-  const int ec0 = 64 * (warp >> 2);
+  const int16_t* lkg = sLk + gj * LS;
+  // epilogue mapping: warp w reads TMEM lanes 32 (w mod 4) + lane = m and
+  // the 8-column chunks ch = w / 4, w / 4 + 2, ... of the pair columns
+  const int em = 32 * (warp & 3) + lane;
+  const int er = em / W, ej = em % W;
+  const int16_t* lke = sLk + ej * LS;
+  float* xrow = sX + er * nstr;
 
   for (int k0 = 0; k0 < nstr && ok; k0 += W) {
-    // ---- link entries of the column strings of this tile, [P][j]
+    // ---- link rows of the column strings of this tile (contiguous in link)
+    const int ncol = min(W, nstr - k0);
     for (int it = tid; it < W * npair; it += TC_THREADS) {
       const int j = it / npair, P = it - j * npair;
-      const int k = k0 + j;
-      sLk[P * WP + j] = k < nstr ? link[k * npair + P] : -1;
+      sLk[j * LS + P] = (int16_t)(j < ncol ? link[(int64_t)k0 * npair + it] : -1);
     }
     __syncthreads();
-    // ---- gather D (column n = r W + j <-> determinant (a0 + r, k0 + j))
+    // ---- gather D^T rows (determinant (a0 + r, k0 + j))
     {
       const int k = k0 + gj;
       const bool col_ok = ga < nstr && k < nstr;
@@ -282,7 +312,7 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad,
               const float x = ccol[(ta >> 1) * nstr];
               v = (ta & 1) ? -x : x;
             }
-            const int32_t tk = sLk[P * WP + gj];
+            const int tk = lkg[P];
             if (tk >= 0) {
               const float x = crow[tk >> 1];
               v += (tk & 1) ? -x : x;
@@ -290,26 +320,26 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad,
           }
           split_bf16(v, h8[q], l8[q]);
         }
-        const uint32_t off = kmajor_offset(gn, pb, kpad);
-        *(uint4*)(sB_hi + off) = *(uint4*)h8;
-        *(uint4*)(sB_lo + off) = *(uint4*)l8;
+        const uint32_t off = kmajor_offset(gm, pb, kpad);
+        *(uint4*)(sD_hi + off) = *(uint4*)h8;
+        *(uint4*)(sD_lo + off) = *(uint4*)l8;
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // ---- MMA: E = g'_hi D_hi + g'_hi D_lo + g'_lo D_hi
+    // ---- MMA: E^T = D_hi g'_hi + D_lo g'_hi + D_hi g'_lo
     if (tid == 0) {
-      const uint32_t ahi = smem_u32(sA_hi), alo = smem_u32(sA_lo);
-      const uint32_t bhi = smem_u32(sB_hi), blo = smem_u32(sB_lo);
+      const uint32_t dhi = smem_u32(sD_hi), dlo = smem_u32(sD_lo);
+      const uint32_t ghi = smem_u32(sG_hi), glo = smem_u32(sG_lo);
       uint32_t acc = 0;
       for (int ks = 0; ks < (kpad >> 4); ks++) {
         const uint32_t koff = (uint32_t)ks * 256u;
-        mma_bf16(tmem, make_desc(ahi + koff, 128, sbo), make_desc(bhi + koff, 128, sbo), idesc, acc);
+        mma_bf16(tmem, make_desc(dhi + koff, 128, sbo), make_desc(ghi + koff, 128, sbo), idesc, acc);
         acc = 1;
-        mma_bf16(tmem, make_desc(ahi + koff, 128, sbo), make_desc(blo + koff, 128, sbo), idesc, 1);
-        mma_bf16(tmem, make_desc(alo + koff, 128, sbo), make_desc(bhi + koff, 128, sbo), idesc, 1);
+        mma_bf16(tmem, make_desc(dlo + koff, 128, sbo), make_desc(ghi + koff, 128, sbo), idesc, 1);
+        mma_bf16(tmem, make_desc(dhi + koff, 128, sbo), make_desc(glo + koff, 128, sbo), idesc, 1);
       }
       mma_commit(&mbar);
     }
@@ -320,21 +350,21 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad,
     }
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // ---- epilogue: E from TMEM, push 1/2 s E into X rows
+    // ---- epilogue: E^T from TMEM, push 1/2 s E into the X row of m
     if (ok) {
-      const int32_t* lk = sLk + eP * WP;
+      const bool m_ok = a0 + er < nstr && ej < ncol;
 #pragma unroll 1
-      for (int cc = 0; cc < 64; cc += 16) {
-        float e[16];
-        tmem_ld16(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(ec0 + cc), e);
-        if (eP < npair) {
+      for (int ch = warp >> 2; ch < nkb; ch += 2) {
+        float e[8];
+        tmem_ld8(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(ch * 8), e);
+        if (m_ok) {
 #pragma unroll
-          for (int q = 0; q < 16; q++) {
-            const int n = ec0 + cc + q;
-            const int r = n / W, j = n % W;
-            if (a0 + r >= nstr) continue;
-            const int32_t t = lk[j];               // -1 for columns beyond nstr
-            if (t >= 0) atomicAdd(&sX[r * nstr + (t >> 1)], (t & 1) ? -0.5f * e[q] : 0.5f * e[q]);
+          for (int q = 0; q < 8; q++) {
+            const int P = ch * 8 + q;
+            if (P < npair) {
+              const int t = lke[P];
+              if (t >= 0) atomicAdd(&xrow[t >> 1], (t & 1) ? -0.5f * e[q] : 0.5f * e[q]);
+            }
           }
         }
       }
@@ -351,7 +381,7 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad,
   }
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
 }
 
 // sigma(a,b) = X(a,b) + X(b,a) + shift (S^2 c)(a,b), FP32 output

@@ -4,7 +4,10 @@ dE/dh and dE/d eri_packed of the whole MBE energy: the MBE-weighted sum of
 the tuples' full-space RDMs (Hellmann-Feynman).  Pinned three ways: against
 the oracle's gradient, against the full-space FCI RDMs for the complete
 unscreened expansion, and against central finite differences of the GPU's
-own energies.  Tolerance 1e-9 (FP64 path; RDM elements are O(1)).
+own energies.  Tolerance 1e-9 (FP64 path; RDM elements are O(1)).  RDMs are
+first order in the CI-vector error (energies are second order), so the
+backward runs converge the Davidson residual to 1e-11 (vector error
+~1e-11 / gap) instead of the default 1e-8.
 """
 import itertools
 
@@ -18,6 +21,7 @@ from oracle import mbe as om
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-9
+TIGHT = dict(conv_tol_r=1e-11, conv_tol_e=1e-14)
 
 
 @pytest.fixture(scope="module")
@@ -29,7 +33,7 @@ def lib():
 
 
 def gpu_grad(lib, h, eri, nocc, ref, exp, max_order, thr, **opts):
-    m = lib.MBE(0, keep_ci=1, **opts)
+    m = lib.MBE(0, keep_ci=1, **{**TIGHT, **opts})
     m.load(h, eri, 2 * nocc)
     res = m.run(ref, exp, max_order, thr)
     dh, dg = m.backward()
@@ -79,7 +83,8 @@ def test_allorder_gradient_is_fci_rdm(lib):
 
 def test_backward_central_fd(lib):
     """Directional derivative of the GPU energy (central differences, step
-    1e-4 along a random symmetric direction) equals <grad, direction>."""
+    1e-6 along a random symmetric direction with O(1) entries in every h and
+    eri element) equals <grad, direction>."""
     n, nocc = 9, 3
     h, eri, _ = ms.gen_integrals(n, nocc, 7)
     ref, exp = [2, 3], [0, 1, 4, 5, 6, 7, 8]
@@ -98,7 +103,7 @@ def test_backward_central_fd(lib):
         m.close()
         return e
 
-    step = 1e-4
+    step = 1e-6
     fd = (energy(step) - energy(-step)) / (2 * step)
     assert abs(fd - an) <= 1e-6 * abs(an) + 1e-8
 
@@ -112,7 +117,8 @@ def test_backward_sharded_contexts_sum(lib):
     h, eri, _ = ms.gen_integrals(n, nocc, 4)
     ref, exp = [2, 3], [0, 1, 4, 5, 6, 7, 8]
     _, dh, dg = gpu_grad(lib, h, eri, nocc, ref, exp, 3, 1e-4)
-    ctxs = [lib.MBE(0, keep_ci=1, backward_share=2), lib.MBE(0, keep_ci=1, backward_share=1)]
+    ctxs = [lib.MBE(0, keep_ci=1, backward_share=2, **TIGHT),
+            lib.MBE(0, keep_ci=1, backward_share=1, **TIGHT)]
     for m in ctxs:
         m.load(h, eri, 2 * nocc)
         lib.mbe_set_reference(m.ctx, ref, exp)
@@ -162,7 +168,7 @@ def test_autograd_function(lib):
     ref, exp = [2, 3], [0, 1, 4, 5, 6, 7]
     ht = torch.tensor(h, requires_grad=True)
     et = torch.tensor(eri, requires_grad=True)
-    e = mbe_energy(ht, et, 2 * nocc, ref, exp, 3)
+    e = mbe_energy(ht, et, 2 * nocc, ref, exp, 3, **TIGHT)
     (2.0 * e).backward()
     tuples = [t for k in range(1, 4) for t in itertools.combinations(exp, k)]
     odh, odg, _ = om.mbe_gradient(h, eri, nocc, ref, tuples)
@@ -175,7 +181,13 @@ def test_grad_workload_fd_sample(lib):
     """8e/20o, CAS(4e,4o) reference over orbitals 2-5, unscreened to order 4
     (2,516 tuples): central differences (step 1e-5) of the GPU energy on a
     seeded sample of unique integrals, and the trace invariant
-    tr dE/dh = N_el (the MBE coefficients sum to one)."""
+    tr dE/dh = N_el (the MBE coefficients sum to one).
+
+    Tolerance 1e-6 |g| + 2e-7: the MBE weights the tuple energies with
+    coefficients up to 1,365 (the reference space) and 364 (order-1 tuples)
+    here, so FP64 rounding of
+    ~1e-15 relative in the ~2,500 tuple energies leaves ~1e-12 Eh of noise in
+    each total energy, i.e. ~1e-7 in a difference quotient with step 1e-5."""
     w = ms.workload("grad_8e20o")
     h, eri, _ = ms.workload_integrals("grad_8e20o")
     nocc, n = w["nocc"], w["norb"]
@@ -200,7 +212,7 @@ def test_grad_workload_fd_sample(lib):
                 M[q, p] += s
         fd = (energy(hp, eri) - energy(hm, eri)) / (2 * step)
         an = dh[p, q] * (1 if p == q else 2)
-        assert abs(fd - an) <= 1e-6 * abs(an) + 1e-8, (p, q, fd, an)
+        assert abs(fd - an) <= 1e-6 * abs(an) + 2e-7, (p, q, fd, an)
     P = ms.npair(n)
     for _ in range(3):
         a, b = sorted(rng.integers(0, P, 2))
@@ -211,4 +223,4 @@ def test_grad_workload_fd_sample(lib):
                 M[b, a] += s
         fd = (energy(h, ep) - energy(h, em)) / (2 * step)
         an = dg[a, b] * (1 if a == b else 2)
-        assert abs(fd - an) <= 1e-6 * abs(an) + 1e-8, (a, b, fd, an)
+        assert abs(fd - an) <= 1e-6 * abs(an) + 2e-7, (a, b, fd, an)

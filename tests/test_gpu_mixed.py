@@ -60,6 +60,29 @@ def test_sigma_tc_elementwise(lib, case, shift):
     m.close()
 
 
+def test_sigma_tc_one_row_per_cta(lib):
+    """12e/14o (3,003 strings, 9.0e6 determinants): above 2,048 strings the
+    tensor-core sigma owns one row of X per CTA.  Too large for the oracle's
+    determinant-driven sigma in test time, so compared with the FP64 GPU
+    sigma, itself pinned to the oracle element by element above."""
+    norb, nocc, seed = 14, 6, 7
+    act = list(range(14))
+    h, eri, _ = ms.gen_integrals(norb, nocc, seed)
+    nstr = 3003
+    c = ms.random_symmetric_ci(nstr, 5)[0]
+    ref_ctx = lib.MBE(0)
+    ref_ctx.load(h, eri, 2 * nocc)
+    ref, ec_ref = lib.mbe_sigma(ref_ctx.ctx, act, c)
+    ref_ctx.close()
+    m = mixed(lib)
+    m.load(h, eri, 2 * nocc)
+    sig, ec = lib.mbe_sigma(m.ctx, act, c)
+    m.close()
+    assert abs(ec - ec_ref) < 1e-12 * max(1.0, abs(ec_ref))
+    scale = np.abs(ref).max()
+    assert np.abs(sig - ref).max() <= 2e-4 * scale
+
+
 def test_mixed_casci_energies_vs_oracle(lib):
     w = ms.workload("h2o_dz_8e23o")
     h, eri, _ = ms.workload_integrals("h2o_dz_8e23o")
