@@ -459,6 +459,101 @@ __global__ void k_scatter_fp64(const int32_t* __restrict__ link, const uint32_t*
   }
 }
 
+// Symmetric c (c(a,b) = c(b,a), the alpha<->beta symmetric Davidson
+// vectors): D and E are symmetric in the two strings, so the beta half of
+// the scatter is the transpose of the alpha half and
+//   sigma = X + X^T + shift S^2 c,  X(a,b) = 1/2 sum_P s_a E_P(J_a, b),
+// with every E read coalesced (row J_a, consecutive b).  k_scatter_sym_fp64
+// writes X into out; k_finish_sym_fp64 adds the transpose (32 x 32 tile
+// pairs in shared memory, in place) and the spin penalty.
+__global__ void k_scatter_sym_fp64(const int32_t* __restrict__ link, int nstr, int npair,
+                                   const double* __restrict__ E, int pair_e,
+                                   const int32_t* __restrict__ active,
+                                   const int32_t* __restrict__ bmap, double* __restrict__ out,
+                                   int64_t out_stride) {
+  const int bl = blockIdx.y;
+  const int b = bmap[bl];
+  if (active && !active[b]) return;
+  const int ndet = nstr * nstr;
+  const double* Eb = E + (int64_t)bl * npair * ndet;
+  double* ob = out + (int64_t)b * out_stride;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ndet; i += gridDim.x * blockDim.x) {
+    const int ia = i / nstr, ib = i - ia * nstr;
+    const int32_t* la = link + (int64_t)ia * npair;
+    double acc = 0.0;
+    for (int P = 0; P < npair; P++) {
+      const int32_t ta = la[P];
+      if (ta >= 0) {
+        const double x = load_e(Eb, (int64_t)P * ndet + (int64_t)(ta >> 1) * nstr + ib, pair_e);
+        acc += (ta & 1) ? -x : x;
+      }
+    }
+    ob[i] = 0.5 * acc;
+  }
+}
+
+__global__ void k_finish_sym_fp64(double* __restrict__ out, int64_t out_stride,
+                                  const int32_t* __restrict__ link,
+                                  const uint32_t* __restrict__ masks, int nstr, int n, int nsig,
+                                  const double* __restrict__ c, int64_t c_stride, double shift,
+                                  const int32_t* __restrict__ active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const int nt = (nstr + 31) / 32;
+  int t = blockIdx.x, I = 0;
+  while (t >= nt - I) {
+    t -= nt - I;
+    I++;
+  }
+  const int J = I + t;
+  __shared__ double sX[2][32][33];
+  double* ob = out + (int64_t)b * out_stride;
+  const double* cb = c + (int64_t)b * c_stride;
+  const int npair = n * (n + 1) / 2;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int h = 0; h < 2; h++) {
+    const int r0 = (h ? J : I) * 32, c0 = (h ? I : J) * 32;
+    for (int i = ty; i < 32; i += blockDim.x >> 5) {
+      const int row = r0 + i, col = c0 + tx;
+      sX[h][i][tx] = (row < nstr && col < nstr) ? ob[(int64_t)row * nstr + col] : 0.0;
+    }
+  }
+  __syncthreads();
+  for (int h = 0; h < 2; h++) {
+    const int r0 = (h ? J : I) * 32, c0 = (h ? I : J) * 32;
+    for (int i = ty; i < 32; i += blockDim.x >> 5) {
+      const int ia = r0 + i, ib = c0 + tx;
+      if (ia >= nstr || ib >= nstr) continue;
+      const int64_t idx = (int64_t)ia * nstr + ib;
+      double v = sX[h][i][tx] + sX[1 - h][tx][i];
+      if (shift != 0.0) {
+        const int32_t* la = link + (int64_t)ia * npair;
+        const int32_t* lb = link + (int64_t)ib * npair;
+        const uint32_t ma = masks[ia], mb = masks[ib];
+        double s2 = (double)(nsig - __popc(ma & mb)) * cb[idx];
+        uint32_t oa = ma & ~mb;
+        const uint32_t obm = mb & ~ma;
+        while (oa) {
+          const int q = __ffs(oa) - 1;
+          oa &= oa - 1;
+          uint32_t o2 = obm;
+          while (o2) {
+            const int p = __ffs(o2) - 1;
+            o2 &= o2 - 1;
+            const int P = p > q ? p * (p + 1) / 2 + q : q * (q + 1) / 2 + p;
+            const int32_t ta = la[P], tb = lb[P];
+            const double x = cb[(int64_t)(ta >> 1) * nstr + (tb >> 1)];
+            s2 -= ((ta ^ tb) & 1) ? -x : x;
+          }
+        }
+        v += shift * s2;
+      }
+      ob[idx] = v;
+    }
+    if (I == J) break;
+  }
+}
+
 __global__ void k_s2(const int32_t* __restrict__ link, const uint32_t* __restrict__ masks,
                      int nstr, int n, int nsig, const double* __restrict__ c, int64_t c_stride,
                      const int32_t* __restrict__ active, double* __restrict__ out,
@@ -495,7 +590,7 @@ __global__ void k_s2(const int32_t* __restrict__ link, const uint32_t* __restric
 
 void sigma_fp64(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const double* c, int64_t c_stride,
                 double* out, int64_t out_stride, const int32_t* active, double spin_shift,
-                bool emulated) {
+                bool emulated, bool symmetric) {
   const int npair = bp.npair;
   if (emulated && !w.err.ptr) {
     w.err.reset(&ctx->pool, 1);
@@ -521,14 +616,15 @@ void sigma_fp64(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const double* c, int
     const int nb = (int)std::min<int64_t>(sb, bp.B - b0);
     sigma_fp64_raw(ctx, bp.n, bp.nsig, bp.nstr, bp.tab->link.ptr, bp.tab->masks.ptr, bp.gp.ptr, c,
                    c_stride, out, out_stride, active, bmap.ptr + b0, nb, w.D.ptr, w.E.ptr,
-                   spin_shift, emulated, w.err.ptr);
+                   spin_shift, emulated, w.err.ptr, symmetric, (int)b0);
   }
 }
 
 void sigma_fp64_raw(mbe_ctx* ctx, int n, int nsig, int nstr, const int32_t* link,
                     const uint32_t* masks, const double* gp, const double* c, int64_t c_stride,
                     double* out, int64_t out_stride, const int32_t* active, const int32_t* bmap,
-                    int nb, double* D, double* E, double spin_shift, bool emulated, int32_t* err) {
+                    int nb, double* D, double* E, double spin_shift, bool emulated, int32_t* err,
+                    bool symmetric, int b_first) {
   const int npair = n * (n + 1) / 2;
   const int64_t ndet = (int64_t)nstr * nstr;
   int64_t blocks = (ndet + 255) / 256;
@@ -556,9 +652,23 @@ void sigma_fp64_raw(mbe_ctx* ctx, int n, int nsig, int nstr, const int32_t* link
   }
   ctx->fp64_timer.end(ctx->stream, ev);
   ctx->stats.fp64_launches += 1;
-  k_scatter_fp64<<<g1, 256, 0, ctx->stream>>>(link, masks, nstr, n, nsig, E, emulated ? 1 : 0, c,
-                                              c_stride, spin_shift, active, bmap, out, out_stride);
-  CU_LAUNCH_CHECK();
+  if (symmetric) {
+    k_scatter_sym_fp64<<<g1, 256, 0, ctx->stream>>>(link, nstr, npair, E, emulated ? 1 : 0,
+                                                    active, bmap, out, out_stride);
+    CU_LAUNCH_CHECK();
+    // the sub-batch is the contiguous tuple range [b_first, b_first + nb)
+    const int ntl = (nstr + 31) / 32;
+    const int b0 = b_first;
+    k_finish_sym_fp64<<<dim3((unsigned)(ntl * (ntl + 1) / 2), nb), 256, 0, ctx->stream>>>(
+        out + (int64_t)b0 * out_stride, out_stride, link, masks, nstr, n, nsig,
+        c + (int64_t)b0 * c_stride, c_stride, spin_shift, active ? active + b0 : nullptr);
+    CU_LAUNCH_CHECK();
+  } else {
+    k_scatter_fp64<<<g1, 256, 0, ctx->stream>>>(link, masks, nstr, n, nsig, E, emulated ? 1 : 0,
+                                                c, c_stride, spin_shift, active, bmap, out,
+                                                out_stride);
+    CU_LAUNCH_CHECK();
+  }
 }
 
 void s2_apply(mbe_ctx* ctx, BinProblem& bp, const double* c, int64_t c_stride, double* out,

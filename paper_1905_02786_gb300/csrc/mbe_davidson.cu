@@ -12,6 +12,7 @@
 // symmetrised.  All tuples of a batch share the subspace size m; a tuple
 // that has converged is frozen (every kernel skips it).
 #include "mbe_internal.cuh"
+#include "mbe_ritz.cuh"
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -87,70 +88,14 @@ __global__ void k_store_grow(const double* __restrict__ dots, int m, int M,
   }
 }
 
-// lowest eigenpair of the m x m symmetric G[b] by cyclic Jacobi (one warp)
+// lowest eigenpair of the m x m subspace matrix G[b] (one warp per tuple)
 __global__ void k_jacobi(const double* __restrict__ G, int m, int M,
-                         const int32_t* __restrict__ active, double* __restrict__ theta,
-                         double* __restrict__ y) {
+                        const int32_t* __restrict__ active, double* __restrict__ theta,
+                        double* __restrict__ y) {
   const int b = blockIdx.x;
   if (!active[b]) return;
-  __shared__ double A[32][33];
-  __shared__ double Z[32][33];
-  const int r = threadIdx.x;
-  for (int i = 0; i < m; i++) {
-    if (r < m) {
-      double a = G[(int64_t)b * M * M + (int64_t)i * M + r];
-      double at = G[(int64_t)b * M * M + (int64_t)r * M + i];
-      A[i][r] = 0.5 * (a + at);
-      Z[i][r] = (i == r) ? 1.0 : 0.0;
-    }
-  }
-  __syncwarp();
-  for (int sweep = 0; sweep < 60; sweep++) {
-    double off = 0.0, dia = 0.0;
-    for (int i = 0; i < m; i++)
-      for (int j = 0; j < m; j++) {
-        if (i != j) off += A[i][j] * A[i][j];
-        else dia += A[i][j] * A[i][j];
-      }
-    if (off <= 1e-30 * dia || off == 0.0) break;
-    for (int p = 0; p < m - 1; p++)
-      for (int q = p + 1; q < m; q++) {
-        double apq = A[p][q];
-        if (fabs(apq) < 1e-300) continue;
-        double app = A[p][p], aqq = A[q][q];
-        double th = (aqq - app) / (2.0 * apq);
-        double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-        double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-        __syncwarp();
-        double arp = 0.0, arq = 0.0, zrp = 0.0, zrq = 0.0;
-        if (r < m) { arp = A[r][p]; arq = A[r][q]; zrp = Z[r][p]; zrq = Z[r][q]; }
-        __syncwarp();
-        if (r < m) {
-          if (r != p && r != q) {
-            double nrp = c * arp - s * arq, nrq = s * arp + c * arq;
-            A[r][p] = nrp; A[p][r] = nrp;
-            A[r][q] = nrq; A[q][r] = nrq;
-          }
-          Z[r][p] = c * zrp - s * zrq;
-          Z[r][q] = s * zrp + c * zrq;
-        }
-        __syncwarp();
-        if (r == 0) {
-          A[p][p] = app - t * apq;
-          A[q][q] = aqq + t * apq;
-          A[p][q] = 0.0;
-          A[q][p] = 0.0;
-        }
-        __syncwarp();
-      }
-  }
-  __syncwarp();
-  int k = 0;
-  double best = A[0][0];
-  for (int i = 1; i < m; i++)
-    if (A[i][i] < best) { best = A[i][i]; k = i; }
-  if (r == 0) theta[b] = best;
-  if (r < m) y[(int64_t)b * M + r] = Z[r][k];
+  __shared__ RitzShared S;
+  ritz_lowest(G + (int64_t)b * M * M, m, M, S, theta + b, y + (int64_t)b * M);
 }
 
 // x = V y, T = AV y - theta x, partial ||T||^2; X receives x.
@@ -499,7 +444,8 @@ void davidson_batch(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int32_t* s
   int total_it = 0;
 
   auto sigma = [&](bool /*unused*/, const double* c, double* out) {
-    sigma_fp64(ctx, bp, sw, c, (int64_t)M * N, out, (int64_t)M * N, active.ptr, shift, emulated);
+    sigma_fp64(ctx, bp, sw, c, (int64_t)M * N, out, (int64_t)M * N, active.ptr, shift, emulated,
+               true);
   };
   // precondition the residual in T, orthogonalise it against V[0..m) and
   // append it as V[m] (tuples whose correction vanished are frozen)

@@ -17,9 +17,10 @@
 //   rounds:  exact point; tuples with |r_x| above the target continue from
 //            {x, t_1, ...} where t_j get tensor-core sigma vectors and the
 //            couplings x.A t_j = theta (x.t_j) + r_x.t_j use only exact data;
-//            the stage stops at max(target, |r_x| / 20).
+//            the stage stops at max(target, |r_x| / 100).
 // The energy error of the reported Rayleigh quotient is below |r_x|^2 / gap.
 #include "mbe_internal.cuh"
+#include "mbe_ritz.cuh"
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -138,72 +139,14 @@ __global__ void k32_store_row(const double* __restrict__ dots, const double* __r
   }
 }
 
-// lowest eigenpair of the m x m symmetric G[b] by cyclic Jacobi (one warp)
+// lowest eigenpair of the m x m subspace matrix G[b] (one warp per tuple)
 __global__ void k32_jacobi(const double* __restrict__ G, int m, int M,
-                           const int32_t* __restrict__ active, double* __restrict__ theta,
-                           double* __restrict__ y) {
+                          const int32_t* __restrict__ active, double* __restrict__ theta,
+                          double* __restrict__ y) {
   const int b = blockIdx.x;
   if (!active[b]) return;
-  __shared__ double A[32][33];
-  __shared__ double Z[32][33];
-  const int r = threadIdx.x;
-  for (int i = 0; i < m; i++)
-    if (r < m) {
-      A[i][r] = 0.5 * (G[(int64_t)b * M * M + (int64_t)i * M + r] +
-                       G[(int64_t)b * M * M + (int64_t)r * M + i]);
-      Z[i][r] = (i == r) ? 1.0 : 0.0;
-    }
-  __syncwarp();
-  for (int sweep = 0; sweep < 40; sweep++) {
-    double off = 0.0, dia = 0.0;
-    if (r < m)
-      for (int j = 0; j < m; j++) {
-        if (j != r) off += A[r][j] * A[r][j];
-        else dia += A[r][j] * A[r][j];
-      }
-    for (int o = 16; o; o >>= 1) {
-      off += __shfl_xor_sync(0xffffffffu, off, o);
-      dia += __shfl_xor_sync(0xffffffffu, dia, o);
-    }
-    if (off <= 1e-30 * dia || off == 0.0) break;
-    for (int p = 0; p < m - 1; p++)
-      for (int q = p + 1; q < m; q++) {
-        const double apq = A[p][q];
-        if (fabs(apq) < 1e-300) continue;
-        const double app = A[p][p], aqq = A[q][q];
-        const double th = (aqq - app) / (2.0 * apq);
-        const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-        __syncwarp();
-        double arp = 0.0, arq = 0.0, zrp = 0.0, zrq = 0.0;
-        if (r < m) { arp = A[r][p]; arq = A[r][q]; zrp = Z[r][p]; zrq = Z[r][q]; }
-        __syncwarp();
-        if (r < m) {
-          if (r != p && r != q) {
-            const double nrp = c * arp - s * arq, nrq = s * arp + c * arq;
-            A[r][p] = nrp; A[p][r] = nrp;
-            A[r][q] = nrq; A[q][r] = nrq;
-          }
-          Z[r][p] = c * zrp - s * zrq;
-          Z[r][q] = s * zrp + c * zrq;
-        }
-        __syncwarp();
-        if (r == 0) {
-          A[p][p] = app - t * apq;
-          A[q][q] = aqq + t * apq;
-          A[p][q] = 0.0;
-          A[q][p] = 0.0;
-        }
-        __syncwarp();
-      }
-  }
-  __syncwarp();
-  int k = 0;
-  double best = A[0][0];
-  for (int i = 1; i < m; i++)
-    if (A[i][i] < best) { best = A[i][i]; k = i; }
-  if (r == 0) theta[b] = best;
-  if (r < m) y[(int64_t)b * M + r] = Z[r][k];
+  __shared__ RitzShared S;
+  ritz_lowest(G + (int64_t)b * M * M, m, M, S, theta + b, y + (int64_t)b * M);
 }
 
 // x = V y; r = AV y - theta x (stage A), or with exact0
@@ -271,26 +214,49 @@ __global__ void k32_converge(const double* __restrict__ partial, int nchunks, in
 }
 
 // t = r / (theta - H_II), symmetrised over (Ia, Ib) <-> (Ib, Ia)
+// 32 x 32 tiles (I, J) and (J, I), I <= J, staged in shared memory so that
+// both the element and its transpose are read and written coalesced
 __global__ void k32_precondition(float* __restrict__ T, const float* __restrict__ hd, int nstr,
                                  const double* __restrict__ theta,
                                  const int32_t* __restrict__ active) {
   const int b = blockIdx.y;
   if (!active[b]) return;
+  // tile pair index -> (I, J), I <= J, row-major over the upper triangle
+  const int nt = (nstr + 31) / 32;
+  int t = blockIdx.x, I = 0;
+  while (t >= nt - I) {
+    t -= nt - I;
+    I++;
+  }
+  const int J = I + t;
+  __shared__ float sT[2][32][33], sH[2][32][33];
   const float th = (float)theta[b];
   const int64_t N = (int64_t)nstr * nstr;
   float* Tb = T + (int64_t)b * N;
   const float* hb = hd + (int64_t)b * N;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    const int ia = (int)(k / nstr), ib = (int)(k % nstr);
-    if (ia > ib) continue;
-    const int64_t kt = (int64_t)ib * nstr + ia;
-    float d1 = th - hb[k], d2 = th - hb[kt];
-    if (fabsf(d1) < 1e-4f) d1 = d1 < 0.f ? -1e-4f : 1e-4f;
-    if (fabsf(d2) < 1e-4f) d2 = d2 < 0.f ? -1e-4f : 1e-4f;
-    const float t = 0.5f * (Tb[k] / d1 + Tb[kt] / d2);
-    Tb[k] = t;
-    Tb[kt] = t;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
+  for (int h = 0; h < 2; h++) {
+    const int r0 = (h ? J : I) * 32, c0 = (h ? I : J) * 32;
+    for (int i = ty; i < 32; i += 8) {
+      const int row = r0 + i, col = c0 + tx;
+      const bool in = row < nstr && col < nstr;
+      sT[h][i][tx] = in ? Tb[(int64_t)row * nstr + col] : 0.f;
+      sH[h][i][tx] = in ? hb[(int64_t)row * nstr + col] : 0.f;
+    }
+  }
+  __syncthreads();
+  // element (I*32 + i, J*32 + j) pairs with (J*32 + j, I*32 + i) = sT[1][j][i]
+  for (int h = 0; h < 2; h++) {
+    const int r0 = (h ? J : I) * 32, c0 = (h ? I : J) * 32;
+    for (int i = ty; i < 32; i += 8) {
+      const int row = r0 + i, col = c0 + tx;
+      if (row >= nstr || col >= nstr) continue;
+      float d1 = th - sH[h][i][tx], d2 = th - sH[1 - h][tx][i];
+      if (fabsf(d1) < 1e-4f) d1 = d1 < 0.f ? -1e-4f : 1e-4f;
+      if (fabsf(d2) < 1e-4f) d2 = d2 < 0.f ? -1e-4f : 1e-4f;
+      Tb[(int64_t)row * nstr + col] = 0.5f * (sT[h][i][tx] / d1 + sT[1 - h][tx][i] / d2);
+    }
+    if (I == J) break;   // a diagonal tile is its own transpose
   }
 }
 
@@ -322,7 +288,10 @@ __global__ void k32_append(const float* __restrict__ T, float* __restrict__ V, i
     if (blockIdx.x == 0 && threadIdx.x == 0) active[b] = 2;
     return;
   }
-  const float inv = (float)(1.0 / sqrt(n2));
+  __shared__ float s_inv;
+  if (threadIdx.x == 0) s_inv = (float)(1.0 / sqrt(n2));   // one FP64 root per block
+  __syncthreads();
+  const float inv = s_inv;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N;
        k += (int64_t)gridDim.x * blockDim.x)
     V[(int64_t)b * M * N + (int64_t)m * N + k] = T[(int64_t)b * N + k] * inv;
@@ -556,7 +525,7 @@ __global__ void k32_select(const double* __restrict__ rnorm, const int32_t* __re
     const double target = fmax(abs_target, rel_target * fmax(1.0, fabs(thx[b])));
     const int a = (mask[b] && rnorm[b] > target) ? 1 : 0;
     active[b] = a;
-    tolr[b] = fmax(target, 0.05 * rnorm[b]);
+    tolr[b] = fmax(target, 0.01 * rnorm[b]);
     if (a) atomicAdd(&cnt, 1);
   }
   __syncthreads();
@@ -594,6 +563,8 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
   cudaStream_t st = ctx->stream;
   const int64_t eb = std::min<int64_t>((N + 255) / 256, 1024);
   const dim3 ge((unsigned)eb, B), gc(nchunks, B);
+  const int ntl = (bp.nstr + 31) / 32;
+  const dim3 gpre((unsigned)(ntl * (ntl + 1) / 2), B);
   const int max_iter = std::max(1, ctx->opt.max_iter);
   int total_it = 0;
   int64_t vecs_tc = 0, vecs_ex = 0;
@@ -643,7 +614,7 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
   };
   // precondition T, orthogonalise against V[0..m) twice, append as V[m]
   auto extend = [&](int m) {
-    k32_precondition<<<ge, 256, 0, st>>>(T.ptr, hd.ptr, bp.nstr, theta.ptr, active.ptr);
+    k32_precondition<<<gpre, 256, 0, st>>>(T.ptr, hd.ptr, bp.nstr, theta.ptr, active.ptr);
     CU_LAUNCH_CHECK();
     for (int pass = 0; pass < 2; pass++) {
       dots(V.ptr, (int64_t)M * N, N, T.ptr, N, m, coef.ptr, M, 1, active.ptr);
@@ -712,7 +683,7 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
     k32_exact_prep<<<ge, 256, 0, st>>>(X.ptr, xx.ptr, V.ptr, M, C64.ptr, N, active.ptr);
     CU_LAUNCH_CHECK();
     dot_comp(V.ptr, (int64_t)M * N, V.ptr, (int64_t)M * N, xx.ptr, active.ptr);
-    sigma_fp64(ctx, bp, sw, C64.ptr, N, S64.ptr, N, active.ptr, shift, true);
+    sigma_fp64(ctx, bp, sw, C64.ptr, N, S64.ptr, N, active.ptr, shift, true, true);
     vecs_ex += B;
     k32_exact_xax<<<gc, RT, 0, st>>>(C64.ptr, S64.ptr, N, nchunks, active.ptr, rpart.ptr);
     CU_LAUNCH_CHECK();

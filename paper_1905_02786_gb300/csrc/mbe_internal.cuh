@@ -209,7 +209,8 @@ void launch_effints_raw(mbe_ctx* ctx, const int32_t* act, int B, int n, int nsig
 void sigma_fp64_raw(mbe_ctx* ctx, int n, int nsig, int nstr, const int32_t* link,
                     const uint32_t* masks, const double* gp, const double* c, int64_t c_stride,
                     double* out, int64_t out_stride, const int32_t* active, const int32_t* bmap,
-                    int nb, double* D, double* E, double spin_shift, bool emulated, int32_t* err);
+                    int nb, double* D, double* E, double spin_shift, bool emulated, int32_t* err,
+                    bool symmetric = false, int b_first = 0);
 StringTables* get_tables(mbe_ctx* ctx, int n, int nsig);
 int count_sig(const mbe_ctx* ctx, const std::vector<int>& act);
 // D[P][K] = (E+_P c)(K) for one CI vector c (ndet) and every packed pair P
@@ -239,9 +240,12 @@ int32_t sigma_tc_error(mbe_ctx* ctx, SigmaWork& w);
 void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host,
                           int32_t* status_host, double* x_out_dev);
 // emulated: the contraction runs as the FP64-grade sliced tensor-core GEMM
+// symmetric: c(a,b) = c(b,a) for every tuple (sigma = X + X^T, coalesced);
+// otherwise any c
 void sigma_fp64(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const double* c,
                 int64_t c_stride, double* out, int64_t out_stride,
-                const int32_t* active, double spin_shift, bool emulated);
+                const int32_t* active, double spin_shift, bool emulated,
+                bool symmetric = false);
 bool ozaki_supported(int npair);
 void contract_ozaki(mbe_ctx* ctx, const double* gp, int npair, const double* D, int64_t ndet,
                     int nb, const int32_t* active, const int32_t* bmap, double* E,

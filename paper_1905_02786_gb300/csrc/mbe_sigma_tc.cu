@@ -135,8 +135,10 @@ struct TcShared {
   uint32_t d_hi, d_lo, g_hi, g_lo, c_rows, x_rows, link_k, link_a, total;
 };
 
-// odd row stride (in int16) of the staged link rows: conflict-free columns
-__host__ __device__ inline int link_stride(int npair) { return npair | 1; }
+// row stride (int16) of the staged link rows: kpad entries (-1 beyond
+// npair) rounded to an odd number of 16-byte units, so that 8-pair blocks
+// are single 16-byte loads and 32 rows read the same block conflict-free
+__host__ __device__ inline int link_stride(int kpad) { return 8 * ((kpad >> 3) | 1); }
 
 __host__ __device__ inline TcShared tc_layout(int kpad, int R, int nstr, int npair, int W) {
   TcShared s;
@@ -152,8 +154,8 @@ __host__ __device__ inline TcShared tc_layout(int kpad, int R, int nstr, int npa
   s.g_lo = take((uint32_t)kpad * kpad * 2);
   s.c_rows = take((uint32_t)R * nstr * 4);
   s.x_rows = take((uint32_t)R * nstr * 4);
-  s.link_k = take((uint32_t)W * link_stride(npair) * 2);
-  s.link_a = take((uint32_t)R * npair * 4);
+  s.link_k = take((uint32_t)2 * W * link_stride(kpad) * 2);
+  s.link_a = take((uint32_t)R * kpad * 4);
   s.total = o;
   return s;
 }
@@ -162,11 +164,6 @@ __host__ __device__ inline uint32_t tmem_cols_for(int kpad) {
   uint32_t c = 32;
   while (c < (uint32_t)kpad) c <<= 1;
   return c;
-}
-
-__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
-  hi = __float2bfloat16_rn(x);
-  lo = __float2bfloat16_rn(x - __bfloat162float(hi));
 }
 
 // Split of g' into bf16 hi + lo in the K-major core-matrix layout, once per
@@ -208,7 +205,7 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad,
            const int32_t* __restrict__ active, float* __restrict__ X, int64_t x_stride,
            int32_t* __restrict__ err) {
   constexpr int W = TC_N / R;
-  const int LS = link_stride(npair);
+  const int LS = link_stride(kpad);
   const int b = blockIdx.y;
   if (active && !active[b]) return;
   const int a0 = blockIdx.x * R;
@@ -224,7 +221,7 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad,
   float* sC = (float*)(smem + L.c_rows);
   float* sX = (float*)(smem + L.x_rows);
   int16_t* sLk = (int16_t*)(smem + L.link_k);     // [j][LS]
-  int32_t* sLa = (int32_t*)(smem + L.link_a);     // [r][P]
+  int32_t* sLa = (int32_t*)(smem + L.link_a);     // [r][kpad]
   const float* cb = c + (int64_t)b * c_stride;
   const uint32_t tcols = tmem_cols_for(kpad);
 
@@ -246,10 +243,10 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad,
     sC[it] = a < nstr ? cb[a * nstr + k] : 0.f;
     sX[it] = 0.f;
   }
-  for (int it = tid; it < R * npair; it += TC_THREADS) {
-    const int r = it / npair, P = it - r * npair;
+  for (int it = tid; it < R * kpad; it += TC_THREADS) {
+    const int r = it / kpad, P = it - r * kpad;
     const int a = a0 + r;
-    sLa[it] = a < nstr ? link[a * npair + P] : -1;
+    sLa[it] = (a < nstr && P < npair) ? link[a * npair + P] : -1;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -276,24 +273,40 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad,
   const int gm = tid & (TC_M - 1);
   const int gr = gm / W, gj = gm % W;            // W is a power of two
   const int ga = a0 + gr;
-  const int32_t* la = sLa + gr * npair;
+  const int32_t* la = sLa + gr * kpad;
   const float* crow = sC + gr * nstr;
-  const int16_t* lkg = sLk + gj * LS;
   // epilogue mapping: warp w reads TMEM lanes 32 (w mod 4) + lane = m and
   // the 8-column chunks ch = w / 4, w / 4 + 2, ... of the pair columns
   const int em = 32 * (warp & 3) + lane;
   const int er = em / W, ej = em % W;
-  const int16_t* lke = sLk + ej * LS;
   float* xrow = sX + er * nstr;
 
-  for (int k0 = 0; k0 < nstr && ok; k0 += W) {
-    // ---- link rows of the column strings of this tile (contiguous in link)
-    const int ncol = min(W, nstr - k0);
-    for (int it = tid; it < W * npair; it += TC_THREADS) {
-      const int j = it / npair, P = it - j * npair;
-      sLk[j * LS + P] = (int16_t)(j < ncol ? link[(int64_t)k0 * npair + it] : -1);
+  // link rows of the column strings of tile kt (contiguous in link) into
+  // buffer buf of sLk, one warp per row
+  auto stage_links = [&](int kt, int buf) {
+    const int nc = min(W, nstr - kt);
+    int16_t* base = sLk + buf * W * LS;
+    for (int j = warp; j < W; j += TC_THREADS / 32) {
+      int16_t* dst = base + j * LS;
+      if (j < nc) {
+        const int32_t* src = link + (int64_t)(kt + j) * npair;
+        int32_t v[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) v[u] = lane + 32 * u < npair ? src[lane + 32 * u] : -1;
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+          if (lane + 32 * u < kpad) dst[lane + 32 * u] = (int16_t)v[u];
+      } else {
+        for (int P = lane; P < kpad; P += 32) dst[P] = (int16_t)-1;
+      }
     }
-    __syncthreads();
+  };
+  stage_links(0, 0);
+  __syncthreads();
+  int cur = 0;
+  for (int k0 = 0; k0 < nstr && ok; k0 += W, cur ^= 1) {
+    const int ncol = min(W, nstr - k0);
+    const int16_t* lkg = sLk + cur * W * LS + gj * LS;
     // ---- gather D^T rows (determinant (a0 + r, k0 + j))
     {
       const int k = k0 + gj;
@@ -301,28 +314,44 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad,
       const float* ccol = cb + k;                 // column k of c, row stride nstr
       for (int kb = tid >> 7; kb < nkb; kb += 2) {
         const int pb = kb * 8;
-        __align__(16) __nv_bfloat16 h8[8], l8[8];
+        // 8 pairs at once: two 16-byte loads of the row link, one of the
+        // column link (entries beyond npair are -1)
+        const int4 a0v = *reinterpret_cast<const int4*>(la + pb);
+        const int4 a1v = *reinterpret_cast<const int4*>(la + pb + 4);
+        const int4 kv = *reinterpret_cast<const int4*>(lkg + pb);
+        const int ta[8] = {a0v.x, a0v.y, a0v.z, a0v.w, a1v.x, a1v.y, a1v.z, a1v.w};
+        const uint32_t kw[4] = {(uint32_t)kv.x, (uint32_t)kv.y, (uint32_t)kv.z, (uint32_t)kv.w};
+        float v[8];
 #pragma unroll
         for (int q = 0; q < 8; q++) {
-          const int P = pb + q;
-          float v = 0.f;
-          if (col_ok && P < npair) {
-            const int32_t ta = la[P];
-            if (ta >= 0) {
-              const float x = ccol[(ta >> 1) * nstr];
-              v = (ta & 1) ? -x : x;
+          v[q] = 0.f;
+          if (col_ok) {
+            if (ta[q] >= 0) {
+              const float x = ccol[(ta[q] >> 1) * nstr];
+              v[q] = (ta[q] & 1) ? -x : x;
             }
-            const int tk = lkg[P];
+            const int tk = (int)(int16_t)(kw[q >> 1] >> (16 * (q & 1)));
             if (tk >= 0) {
               const float x = crow[tk >> 1];
-              v += (tk & 1) ? -x : x;
+              v[q] += (tk & 1) ? -x : x;
             }
           }
-          split_bf16(v, h8[q], l8[q]);
+        }
+        // split into bf16 hi + lo, two values per conversion
+        uint4 hv, lv;
+        uint32_t* hw = &hv.x;
+        uint32_t* lw = &lv.x;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+          const float2 hf = __bfloat1622float2(h2);
+          const __nv_bfloat162 l2 = __floats2bfloat162_rn(v[2 * q] - hf.x, v[2 * q + 1] - hf.y);
+          hw[q] = *reinterpret_cast<const uint32_t*>(&h2);
+          lw[q] = *reinterpret_cast<const uint32_t*>(&l2);
         }
         const uint32_t off = kmajor_offset(gm, pb, kpad);
-        *(uint4*)(sD_hi + off) = *(uint4*)h8;
-        *(uint4*)(sD_lo + off) = *(uint4*)l8;
+        *(uint4*)(sD_hi + off) = hv;
+        *(uint4*)(sD_lo + off) = lv;
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -343,6 +372,9 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad,
       }
       mma_commit(&mbar);
     }
+    // the next tile's link rows load while the MMA runs (the other buffer is
+    // free: its last reader, the previous epilogue, ended at a barrier)
+    if (k0 + W < nstr) stage_links(k0 + W, cur ^ 1);
     const int timed_out = mbar_wait(&mbar, phase) ? 0 : 1;
     if (__syncthreads_or(timed_out)) {
       ok = false;
@@ -353,18 +385,18 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad,
     // ---- epilogue: E^T from TMEM, push 1/2 s E into the X row of m
     if (ok) {
       const bool m_ok = a0 + er < nstr && ej < ncol;
+      const int16_t* lke = sLk + cur * W * LS + ej * LS;
 #pragma unroll 1
       for (int ch = warp >> 2; ch < nkb; ch += 2) {
         float e[8];
         tmem_ld8(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(ch * 8), e);
         if (m_ok) {
+          const int4 kv = *reinterpret_cast<const int4*>(lke + ch * 8);
+          const uint32_t kw[4] = {(uint32_t)kv.x, (uint32_t)kv.y, (uint32_t)kv.z, (uint32_t)kv.w};
 #pragma unroll
           for (int q = 0; q < 8; q++) {
-            const int P = ch * 8 + q;
-            if (P < npair) {
-              const int t = lke[P];
-              if (t >= 0) atomicAdd(&xrow[t >> 1], (t & 1) ? -0.5f * e[q] : 0.5f * e[q]);
-            }
+            const int t = (int)(int16_t)(kw[q >> 1] >> (16 * (q & 1)));
+            if (t >= 0) atomicAdd(&xrow[t >> 1], (t & 1) ? -0.5f * e[q] : 0.5f * e[q]);
           }
         }
       }
