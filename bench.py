@@ -163,6 +163,43 @@ def transfer_bytes(res, h, eri):
     return h2d, d2h
 
 
+def run_profile_batch(args):
+    """One mixed batch of seeded order-6 tuples of the 8e/23o workload (all
+    with orbital 0: 8e/12o CASCIs, 245,025 determinants; or, with
+    --profile-small, all without it: 6e/12o, 48,400), solved inside the NVTX
+    range 'solve' after the reference space is set up, so that
+    `ncu --nvtx --nvtx-include solve/` captures exactly this batch."""
+    import torch
+    from paper_1905_02786_gb300 import build, _binding as B
+    build.build()
+    B.load_library()
+    name = "h2o_dz_8e23o"
+    w = ms.workload(name)
+    h, eri, _ = ms.workload_integrals(name)
+    m = B.MBE(0, precision=B.MBE_MIXED_BF16X3, max_batch=4096, timing=1)
+    m.load(h, eri, w["nel"])
+    B.mbe_set_reference(m.ctx, w["ref"], w["exp"])
+    rest = [o for o in w["exp"] if o != 0]
+    n = args.profile_batch
+    if args.profile_small:
+        tuples = np.array(ms.sample_tuples(rest, 6, n, 13), dtype=np.int32)
+    else:
+        tuples = np.array([(0,) + t for t in ms.sample_tuples(rest, 5, n, 12)], dtype=np.int32)
+    B.mbe_reset_stats(m.ctx)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("solve")
+    t0 = time.perf_counter()
+    B.mbe_solve_tuples(m.ctx, tuples, 6)
+    dt = time.perf_counter() - t0
+    torch.cuda.nvtx.range_pop()
+    st = B.mbe_get_stats(m.ctx)
+    print(json.dumps({"profile_batch": n, "cas": "6e/12o" if args.profile_small else "8e/12o",
+                      "seconds": dt, "tuples_per_s": n / dt,
+                      "tc_tflops": st["dom_flops"] / st["dom_ms"] / 1e9 if st["dom_ms"] else None,
+                      "stats": st}))
+    m.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -175,9 +212,18 @@ def main():
     ap.add_argument("--max-batch", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--profile-batch", type=int, default=0,
+                    help="profiling case instead of the bench: solve this many seeded "
+                         "order-6 tuples of the workload as one batch inside the NVTX "
+                         "range 'solve' and print its counters")
+    ap.add_argument("--profile-small", action="store_true",
+                    help="with --profile-batch: tuples without orbital 0 (6e/12o "
+                         "CASCIs) instead of tuples with it (8e/12o)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_batch:
+        return run_profile_batch(args)
 
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -231,11 +277,13 @@ def main():
         for _ in range(args.steps):
             flush.fill_(1.0)
             ea, eb, ec = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            torch.cuda.nvtx.range_push("timed_step")
             ea.record(stream)
             m.load(h, eri, w["nel"])
             eb.record(stream)
             res = step()
             ec.record(stream)
+            torch.cuda.nvtx.range_pop()
             ntup += res["ntup"]
             ec.synchronize()
             t_ms += eb.elapsed_time(ec)

@@ -280,23 +280,33 @@ k_contract_ozaki(const double* __restrict__ gp_all, int npair, int kpad,
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     // ---- epilogue: E = 2^(e_P + e_n - 54) I with the exact integer
-    // I = sum_s acc_s 2^(8 (5 - s)) (|I| < 2^62), stored as the float pair
-    // (hi, lo) = (fl(I), I - fl(I)) scaled by 2^(e_P + e_n - 54)
+    // I = sum_s acc_s 2^(8 (5 - s)) (|I| < 2^62).  Every acc_s is an exact
+    // FP32 integer and every acc_s 2^(8 (5 - s)) an exact FP32 value, so I is
+    // summed with error-free FP32 transformations (TwoSum, largest group
+    // first): I = S + Err exactly, with Err summed in FP32 (relative error
+    // ~2^-48 of |I|); (hi, lo) = FastTwoSum(S, Err).  No 64-bit integer or
+    // FP64 operation: those run on GB300's small FP64 pipe.
     {
       const int P = 32 * (warp & 3) + lane;
       const int c0 = 32 * (warp >> 2);
       const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
       for (int cc = 0; cc < 32; cc += 16) {
-        long long I[16];
+        float S[16], Er[16];
 #pragma unroll
-        for (int q = 0; q < 16; q++) I[q] = 0;
+        for (int q = 0; q < 16; q++) S[q] = Er[q] = 0.f;
 #pragma unroll
         for (int sgrp = 0; sgrp < OZ_GROUPS; sgrp++) {
           float v[16];
           tmem_ld16(tmem + lane_off + (uint32_t)(sgrp * OZ_N + c0 + cc), v);
+          const float w = __int_as_float((127 + 8 * (OZ_GROUPS - 1 - sgrp)) << 23);   // 2^(8(5-s))
 #pragma unroll
-          for (int q = 0; q < 16; q++)
-            I[q] += (long long)__float2ll_rn(v[q]) << (8 * (OZ_GROUPS - 1 - sgrp));
+          for (int q = 0; q < 16; q++) {
+            const float t = v[q] * w;                 // exact
+            const float sn = S[q] + t;
+            const float bb = sn - S[q];
+            Er[q] += (S[q] - (sn - bb)) + (t - bb);
+            S[q] = sn;
+          }
         }
         if (P < npair) {
 #pragma unroll
@@ -304,8 +314,8 @@ k_contract_ozaki(const double* __restrict__ gp_all, int npair, int kpad,
             const int n = c0 + cc + q;
             const int64_t col = n0 + n;
             if (col < ndet) {
-              const float hi = __ll2float_rn(I[q]);
-              const float lo = __ll2float_rn(I[q] - __float2ll_rn(hi));
+              const float hi = S[q] + Er[q];
+              const float lo = Er[q] - (hi - S[q]);
               const int k = sEa[P] + sEb[n] - 14 - 8 * (OZ_GROUPS - 1);
               float2 o;
               o.x = ldexpf(hi, k);
