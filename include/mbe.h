@@ -93,6 +93,15 @@ typedef struct mbe_options {
                            holds (tuples sharded over contexts); 2 as 1 plus
                            the reference-space term (exactly one context of
                            a sharded run)                                    */
+  int warm_start;       /* 1: a tuple starts its Davidson iteration from the
+                           converged vector of a parent (the tuple less one
+                           orbital, solved at the previous order) with the
+                           orbital added; 0 (default): from the lowest
+                           diagonal determinant.  A parent state can overlap
+                           an excited state of the child more than its
+                           ground state, so the iteration can settle on the
+                           wrong root; measured on the 8e/23o workload it
+                           saved few iterations.                             */
 } mbe_options;
 
 typedef struct mbe_ctx mbe_ctx;
@@ -119,7 +128,7 @@ typedef struct mbe_stats {
 
 /* Fill *opt with the defaults (FP64, max_batch 256, subspace 16, 200
  * iterations, tol_r 1e-8, tol_e 1e-12, spin_shift 0.5, keep_ci 0,
- * deterministic 1, no memory cap). */
+ * deterministic 1, no memory cap, warm_start 0). */
 void mbe_default_options(mbe_options* opt);
 
 /* Create a context on CUDA device `device`.  opt may be NULL (defaults).

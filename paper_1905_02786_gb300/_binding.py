@@ -41,7 +41,7 @@ class mbe_options(ctypes.Structure):
                 ("spin_shift", ctypes.c_double), ("keep_ci", ctypes.c_int),
                 ("deterministic", ctypes.c_int), ("mem_cap_bytes", ctypes.c_int64),
                 ("timing", ctypes.c_int), ("verbose", ctypes.c_int),
-                ("backward_share", ctypes.c_int)]
+                ("backward_share", ctypes.c_int), ("warm_start", ctypes.c_int)]
 
 
 _lib = None

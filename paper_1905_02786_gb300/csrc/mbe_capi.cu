@@ -119,9 +119,35 @@ int count_sig(const mbe_ctx* ctx, const std::vector<int>& act) {
 
 namespace {
 
-// Solve the CASCI of every active space in `acts`; binned by (n, nsig).
+std::pair<uint64_t, uint64_t> orbital_key(const std::vector<int>& orbs) {
+  uint64_t k0 = 0, k1 = 0;
+  for (int o : orbs) {
+    if (o < 64) k0 |= 1ull << o;
+    else k1 |= 1ull << (o - 64);
+  }
+  return {k0, k1};
+}
+
+// Solve the CASCI of every active space in `acts` (the tuples of one order,
+// or the reference space as order 0); binned by (n, nsig).  With warm starts
+// on, a tuple whose parent (the tuple less one orbital) was solved at the
+// previous order starts from that vector, and the converged vectors of this
+// call are kept for the next order.
 void solve_jobs(mbe_ctx* ctx, const std::vector<std::vector<int>>& acts, double* eps,
-                int32_t* status, std::vector<std::vector<double>>* ci_out) {
+                int32_t* status, std::vector<std::vector<double>>* ci_out, int order) {
+  const bool warm = ctx->opt.warm_start != 0;
+  if (warm) {
+    if (ctx->guess_cur.order == order - 1) {
+      std::swap(ctx->guess_prev, ctx->guess_cur);
+      ctx->guess_cur.clear();
+    } else if (ctx->guess_cur.order != order) {
+      ctx->guess_prev.clear();
+      ctx->guess_cur.clear();
+    }
+    ctx->guess_cur.order = order;
+  }
+  std::vector<char> is_ref(ctx->norb, 0);
+  for (int r : ctx->ref) is_ref[r] = 1;
   std::map<std::pair<int, int>, std::vector<int64_t>> bins;
   for (int64_t j = 0; j < (int64_t)acts.size(); j++) {
     int n = (int)acts[j].size();
@@ -160,16 +186,54 @@ void solve_jobs(mbe_ctx* ctx, const std::vector<std::vector<int>>& acts, double*
       CU_CHECK(cudaMemcpyAsync(bp.act.ptr, act_h.data(), sizeof(int32_t) * act_h.size(),
                                cudaMemcpyHostToDevice, ctx->stream));
       launch_effints(ctx, bp);
+      // warm-start plan: the first parent found in the previous order's store
+      GuessPlan plan;
+      if (warm && order >= 1 && ctx->guess_prev.order == order - 1)
+        for (int b = 0; b < B; b++) {
+          const std::vector<int>& act = acts[idx[c0 + b]];
+          std::vector<int> tup;
+          for (int o : act)
+            if (!is_ref[o]) tup.push_back(o);
+          for (int r = (int)tup.size() - 1; r >= 0; r--) {
+            std::vector<int> par(tup);
+            par.erase(par.begin() + r);
+            auto it = ctx->guess_prev.map.find(orbital_key(par));
+            if (it == ctx->guess_prev.map.end()) continue;
+            const int o = tup[r];
+            plan.b.push_back(b);
+            plan.jo.push_back((int)(std::lower_bound(act.begin(), act.end(), o) - act.begin()));
+            plan.occ.push_back(o < ctx->nocc ? 1 : 0);
+            plan.src.push_back(it->second);
+            break;
+          }
+        }
+      // keep this batch's vectors for the next order if they fit the cap
+      const int64_t keep_bytes = (int64_t)B * N * 4;
+      const bool keep = warm && ctx->guess_cur.bytes + keep_bytes <= (int64_t)(0.25 * budget);
       DevBuf<double> X;
-      if (ci_out) X.reset(&ctx->pool, (size_t)B * N);
+      if (ci_out || keep) X.reset(&ctx->pool, (size_t)B * N);
       std::vector<double> e(B);
       std::vector<int32_t> s(B);
       const bool mixed = ctx->opt.precision == MBE_MIXED_BF16X3 && N > 1 &&
                          sigma_tc_supported(n, tab->nstr) && ozaki_supported(tab->npair);
+      const GuessPlan* pp = plan.b.empty() ? nullptr : &plan;
       if (mixed)
-        davidson_batch_mixed(ctx, bp, e.data(), s.data(), ci_out ? X.ptr : nullptr);
+        davidson_batch_mixed(ctx, bp, e.data(), s.data(), X.ptr, pp);
       else
-        davidson_batch(ctx, bp, e.data(), s.data(), nullptr, ci_out ? X.ptr : nullptr);
+        davidson_batch(ctx, bp, e.data(), s.data(), nullptr, X.ptr, pp);
+      if (keep) {
+        auto blk = std::make_unique<DevBuf<float>>(&ctx->pool, (size_t)B * N);
+        convert_f64_to_f32(ctx, X.ptr, blk->ptr, (int64_t)B * N);
+        for (int b = 0; b < B; b++) {
+          const std::vector<int>& act = acts[idx[c0 + b]];
+          std::vector<int> tup;
+          for (int o : act)
+            if (!is_ref[o]) tup.push_back(o);
+          ctx->guess_cur.map[orbital_key(tup)] = blk->ptr + (int64_t)b * N;
+        }
+        ctx->guess_cur.blocks.push_back(std::move(blk));
+        ctx->guess_cur.bytes += keep_bytes;
+      }
       for (int b = 0; b < B; b++) {
         if (eps) eps[idx[c0 + b]] = e[b];
         if (status) status[idx[c0 + b]] = s[b];
@@ -214,6 +278,7 @@ void mbe_default_options(mbe_options* o) {
   o->timing = 0;
   o->verbose = 0;
   o->backward_share = 0;
+  o->warm_start = 0;
 }
 
 int mbe_create(mbe_ctx** out, int device, const mbe_options* opt) {
@@ -294,6 +359,8 @@ int mbe_load_integrals(mbe_ctx* ctx, int norb, int nelec, const double* h, const
     ctx->have_ref = false;
     ctx->kept.clear();
     ctx->kept_ref = false;
+    ctx->guess_prev.clear();
+    ctx->guess_cur.clear();
     ctx->last_order = 0;
     ctx->cur_order = 0;
     ctx->order_sums.clear();
@@ -322,12 +389,14 @@ int mbe_set_reference(mbe_ctx* ctx, const int* ref_orbs, int nref, const int* ex
     std::sort(ctx->ref.begin(), ctx->ref.end());
     ctx->exp.assign(exp_orbs, exp_orbs + nexp);
     std::sort(ctx->exp.begin(), ctx->exp.end());
-    // order 0: the CASCI of the reference space
+    // order 0: the CASCI of the reference space (a fresh warm-start chain)
+    ctx->guess_prev.clear();
+    ctx->guess_cur.clear();
     double e = 0.0;
     int32_t st = 0;
     std::vector<std::vector<double>> ci;
     if (nref > 0) {
-      solve_jobs(ctx, {ctx->ref}, &e, &st, ctx->opt.keep_ci ? &ci : nullptr);
+      solve_jobs(ctx, {ctx->ref}, &e, &st, ctx->opt.keep_ci ? &ci : nullptr, 0);
     } else {
       // empty reference: the inactive-core energy of the closed-shell determinant
       double ec = 0.0;
@@ -388,7 +457,7 @@ int mbe_solve_tuples(mbe_ctx* ctx, int order, const int32_t* tuples, int64_t ntu
     std::vector<double> eps(ntup);
     std::vector<int32_t> st(ntup, 0);
     std::vector<std::vector<double>> ci;
-    solve_jobs(ctx, acts, eps.data(), st.data(), ctx->opt.keep_ci ? &ci : nullptr);
+    solve_jobs(ctx, acts, eps.data(), st.data(), ctx->opt.keep_ci ? &ci : nullptr, order);
     ctx->cur_order = order;
     ctx->cur_tuples.assign(tuples, tuples + ntup * order);
     ctx->cur_eps = eps;

@@ -691,3 +691,124 @@ void gather_d_fp64(mbe_ctx* ctx, const StringTables* tab, const double* c, doubl
       tab->link.ptr, tab->nstr, tab->npair, c, ndet, nullptr, bmap.ptr, D);
   CU_LAUNCH_CHECK();
 }
+
+// ------------------------------------------------------------ warm starts
+namespace {
+
+__global__ void k_f64_to_f32(const double* __restrict__ src, float* __restrict__ dst, int64_t n) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    dst[k] = (float)src[k];
+}
+
+// V[b][0] of the child tuple from the parent's vector: every parent string
+// (n - 1 orbitals) gains the added orbital at active position jo -- empty,
+// or occupied in both strings, which moves its creation operators past the
+// electrons below it: sign (-1)^(n_alpha below + n_beta below).  The child
+// row is zeroed first by k_zero_start.
+template <typename T>
+__global__ void k_zero_start(const int32_t* __restrict__ bidx, int64_t N, T* __restrict__ V,
+                             int64_t vstride) {
+  T* Vb = V + (int64_t)bidx[blockIdx.y] * vstride;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N;
+       k += (int64_t)gridDim.x * blockDim.x)
+    Vb[k] = (T)0;
+}
+
+template <typename T>
+__global__ void k_parent_guess(const float* const* __restrict__ src,
+                               const int32_t* __restrict__ bidx, const int32_t* __restrict__ jo,
+                               const int32_t* __restrict__ occ,
+                               const uint32_t* __restrict__ masks_v, int nstr_v,
+                               const uint32_t* __restrict__ masks_o, int nstr_o, int nstr,
+                               T* __restrict__ V, int64_t vstride) {
+  const int e = blockIdx.y;
+  const int o = occ[e], j = jo[e];
+  const uint32_t* pm = o ? masks_o : masks_v;
+  const int np = o ? nstr_o : nstr_v;
+  const int64_t Np = (int64_t)np * np;
+  const uint32_t low = (1u << j) - 1u;
+  const float* sv = src[e];
+  T* Vb = V + (int64_t)bidx[e] * vstride;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int ia = (int)(i / np), ib = (int)(i - (int64_t)ia * np);
+    const uint32_t ma = pm[ia], mb = pm[ib];
+    const uint32_t ca = (ma & low) | ((ma & ~low) << 1) | ((uint32_t)o << j);
+    const uint32_t cb = (mb & low) | ((mb & ~low) << 1) | ((uint32_t)o << j);
+    const int neg = o ? ((__popc(ma & low) + __popc(mb & low)) & 1) : 0;
+    const float v = sv[i];
+    Vb[(int64_t)mask_rank(ca) * nstr + mask_rank(cb)] = (T)(neg ? -v : v);
+  }
+}
+
+// the inserted vectors are FP32 copies: normalise each in FP64 (the
+// Rayleigh-Ritz step assumes an orthonormal basis), one block per tuple
+template <typename T>
+__global__ void k_normalize_start(const int32_t* __restrict__ bidx, int64_t N, T* __restrict__ V,
+                                  int64_t vstride) {
+  T* Vb = V + (int64_t)bidx[blockIdx.x] * vstride;
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int64_t k = threadIdx.x; k < N; k += blockDim.x) s += (double)Vb[k] * (double)Vb[k];
+  for (int off = 16; off; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  __shared__ double inv;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
+    inv = t > 0.0 ? 1.0 / sqrt(t) : 1.0;
+  }
+  __syncthreads();
+  for (int64_t k = threadIdx.x; k < N; k += blockDim.x) Vb[k] = (T)((double)Vb[k] * inv);
+}
+
+}  // namespace
+
+void launch_parent_guess(mbe_ctx* ctx, const GuessPlan& plan, int n, int nsig, int nstr,
+                         float* V32, double* V64, int64_t vstride) {
+  const int ne = (int)plan.b.size();
+  if (ne == 0 || n < 2) return;
+  bool any_o = false, any_v = false;
+  for (int e = 0; e < ne; e++) (plan.occ[e] ? any_o : any_v) = true;
+  const StringTables* tv = any_v ? get_tables(ctx, n - 1, nsig) : nullptr;
+  const StringTables* to = (any_o && nsig >= 1) ? get_tables(ctx, n - 1, nsig - 1) : nullptr;
+  if (any_o && !to) throw MbeError{MBE_ESTATE, "occupied added orbital without electrons"};
+  DevBuf<int32_t> bidx(&ctx->pool, ne), jo(&ctx->pool, ne), occ(&ctx->pool, ne);
+  DevBuf<const float*> src(&ctx->pool, ne);
+  cudaStream_t st = ctx->stream;
+  CU_CHECK(cudaMemcpyAsync(bidx.ptr, plan.b.data(), sizeof(int32_t) * ne, cudaMemcpyHostToDevice, st));
+  CU_CHECK(cudaMemcpyAsync(jo.ptr, plan.jo.data(), sizeof(int32_t) * ne, cudaMemcpyHostToDevice, st));
+  CU_CHECK(cudaMemcpyAsync(occ.ptr, plan.occ.data(), sizeof(int32_t) * ne, cudaMemcpyHostToDevice, st));
+  CU_CHECK(cudaMemcpyAsync(src.ptr, plan.src.data(), sizeof(const float*) * ne,
+                           cudaMemcpyHostToDevice, st));
+  const int64_t N = (int64_t)nstr * nstr;
+  const dim3 g((unsigned)std::min<int64_t>((N + 255) / 256, 1024), ne);
+  const uint32_t* mv = tv ? tv->masks.ptr : nullptr;
+  const uint32_t* mo = to ? to->masks.ptr : nullptr;
+  const int nv = tv ? tv->nstr : 0, no = to ? to->nstr : 0;
+  if (V32) {
+    k_zero_start<float><<<g, 256, 0, st>>>(bidx.ptr, N, V32, vstride);
+    CU_LAUNCH_CHECK();
+    k_parent_guess<float><<<g, 256, 0, st>>>(src.ptr, bidx.ptr, jo.ptr, occ.ptr, mv, nv, mo, no,
+                                             nstr, V32, vstride);
+    CU_LAUNCH_CHECK();
+    k_normalize_start<float><<<ne, 1024, 0, st>>>(bidx.ptr, N, V32, vstride);
+  } else {
+    k_zero_start<double><<<g, 256, 0, st>>>(bidx.ptr, N, V64, vstride);
+    CU_LAUNCH_CHECK();
+    k_parent_guess<double><<<g, 256, 0, st>>>(src.ptr, bidx.ptr, jo.ptr, occ.ptr, mv, nv, mo, no,
+                                              nstr, V64, vstride);
+    CU_LAUNCH_CHECK();
+    k_normalize_start<double><<<ne, 1024, 0, st>>>(bidx.ptr, N, V64, vstride);
+  }
+  CU_LAUNCH_CHECK();
+}
+
+void convert_f64_to_f32(mbe_ctx* ctx, const double* src, float* dst, int64_t n) {
+  if (n <= 0) return;
+  k_f64_to_f32<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, ctx->stream>>>(
+      src, dst, n);
+  CU_LAUNCH_CHECK();
+}

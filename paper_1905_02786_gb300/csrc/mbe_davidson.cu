@@ -404,7 +404,7 @@ struct Multidot {
 // Davidson for one batch of tuples: one stage with FP64 (or emulated-FP64)
 // sigma vectors to conv_tol_r / conv_tol_e.
 void davidson_batch(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int32_t* status_host,
-                    double* s2_host, double* x_out_dev) {
+                    double* s2_host, double* x_out_dev, const GuessPlan* plan) {
   const int B = bp.B;
   const int M = std::max(4, std::min(32, ctx->opt.max_subspace));
   const int64_t N = bp.ndet;
@@ -428,6 +428,7 @@ void davidson_batch(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int32_t* s
   launch_hdiag(ctx, bp, shift, hd.ptr);
   k_guess<<<B, 256, 0, st>>>(hd.ptr, bp.nstr, M, V.ptr);
   CU_LAUNCH_CHECK();
+  if (plan) launch_parent_guess(ctx, *plan, bp.n, bp.nsig, bp.nstr, nullptr, V.ptr, (int64_t)M * N);
   k_set_i32<<<1, 256, 0, st>>>(active.ptr, B, 1);
   CU_LAUNCH_CHECK();
   CU_CHECK(cudaMemsetAsync(iters.ptr, 0, sizeof(int32_t) * B, st));

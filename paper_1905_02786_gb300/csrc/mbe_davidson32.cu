@@ -545,7 +545,7 @@ __global__ void k32_copy_i(const int32_t* s, int32_t* d, int n) {
 }  // namespace
 
 void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int32_t* status_host,
-                          double* x_out_dev) {
+                          double* x_out_dev, const GuessPlan* plan) {
   const int B = bp.B;
   const int M = std::max(4, std::min(32, ctx->opt.max_subspace));
   const int64_t N = bp.ndet;
@@ -575,6 +575,7 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
   CU_LAUNCH_CHECK();
   k32_guess<<<B, 256, 0, st>>>(hd.ptr, bp.nstr, M, V.ptr);
   CU_LAUNCH_CHECK();
+  if (plan) launch_parent_guess(ctx, *plan, bp.n, bp.nsig, bp.nstr, V.ptr, nullptr, (int64_t)M * N);
   k32_fill_i<<<1, 256, 0, st>>>(active.ptr, B, 1);
   CU_LAUNCH_CHECK();
   CU_CHECK(cudaMemsetAsync(iters.ptr, 0, sizeof(int32_t) * B, st));

@@ -5,6 +5,7 @@
 #include <string>
 #include <vector>
 #include <map>
+#include <memory>
 #include <unordered_map>
 #include "../../include/mbe.h"
 
@@ -129,6 +130,35 @@ struct HashTable {
   DevBuf<int32_t> state;       // 0 empty, 1 claimed/filled
 };
 
+// Warm starts: the converged CI vectors (FP32) of the tuples solved at one
+// order, keyed by tuple (128-bit orbital set); a tuple of the next order
+// starts its Davidson iteration from a parent's vector with the added
+// orbital inserted (empty, or doubly occupied with its fermion sign).
+struct KeyHash {
+  size_t operator()(const std::pair<uint64_t, uint64_t>& k) const {
+    return (size_t)(k.first * 0x9E3779B97F4A7C15ull ^ (k.second + 0x632BE59BD9B4E019ull +
+                                                         (k.first << 6) + (k.first >> 2)));
+  }
+};
+struct GuessStore {
+  int order = -1;
+  std::vector<std::unique_ptr<DevBuf<float>>> blocks;
+  std::unordered_map<std::pair<uint64_t, uint64_t>, const float*, KeyHash> map;
+  int64_t bytes = 0;
+  void clear() {
+    map.clear();
+    blocks.clear();
+    bytes = 0;
+    order = -1;
+  }
+};
+// tuples b of a batch that start from a parent vector src, the added
+// orbital at active position jo, occupied (occ = 1) or empty
+struct GuessPlan {
+  std::vector<int32_t> b, jo, occ;
+  std::vector<const float*> src;
+};
+
 struct OrderRec {
   int order;
   std::vector<int32_t> tuples;   // ntup * order
@@ -178,6 +208,8 @@ struct mbe_ctx {
   std::vector<KeptCI> kept;
   bool kept_ref = false;
   KeptCI ref_ci;
+  // warm-start vectors of the previous and the current order
+  GuessStore guess_prev, guess_cur;
 
   ~mbe_ctx();
 };
@@ -238,7 +270,12 @@ void sigma_tc(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const float* c, int64_
 int32_t sigma_tc_error(mbe_ctx* ctx, SigmaWork& w);
 // Davidson of the mixed-precision mode: FP32 vectors, FP64-grade exact points
 void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host,
-                          int32_t* status_host, double* x_out_dev);
+                          int32_t* status_host, double* x_out_dev, const GuessPlan* plan);
+void convert_f64_to_f32(mbe_ctx* ctx, const double* src, float* dst, int64_t n);
+// overwrite the start vectors V[b] (stride vstride) of the planned tuples
+// with their parents' vectors (exactly one of V32 / V64 non-null)
+void launch_parent_guess(mbe_ctx* ctx, const GuessPlan& plan, int n, int nsig, int nstr,
+                         float* V32, double* V64, int64_t vstride);
 // emulated: the contraction runs as the FP64-grade sliced tensor-core GEMM
 // symmetric: c(a,b) = c(b,a) for every tuple (sigma = X + X^T, coalesced);
 // otherwise any c
@@ -256,7 +293,8 @@ void s2_apply(mbe_ctx* ctx, BinProblem& bp, const double* c, int64_t c_stride,
 // Davidson for a batch; writes e_out (B, total energies incl. core),
 // status (B), s2 (B), and, if x_out != NULL, the converged vectors (B*ndet).
 void davidson_batch(mbe_ctx* ctx, BinProblem& bp, double* e_out_host,
-                    int32_t* status_host, double* s2_host, double* x_out_dev);
+                    int32_t* status_host, double* s2_host, double* x_out_dev,
+                    const GuessPlan* plan = nullptr);
 
 // hash / increments
 void hash_init(mbe_ctx* ctx, int64_t cap);

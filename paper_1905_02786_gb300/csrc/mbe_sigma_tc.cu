@@ -104,20 +104,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t phase) {
   return false;
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
-}
-
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
   uint32_t r[8];
   asm volatile(
@@ -152,7 +138,7 @@ __host__ __device__ inline TcShared tc_layout(int kpad, int R, int nstr, int npa
   s.d_lo = take((uint32_t)TC_M * kpad * 2);
   s.g_hi = take((uint32_t)kpad * kpad * 2);
   s.g_lo = take((uint32_t)kpad * kpad * 2);
-  s.c_rows = take((uint32_t)R * nstr * 4);
+  s.c_rows = take((uint32_t)R * (nstr + 1) * 4);
   s.x_rows = take((uint32_t)R * nstr * 4);
   s.link_k = take((uint32_t)2 * W * link_stride(kpad) * 2);
   s.link_a = take((uint32_t)R * kpad * 4);
@@ -220,7 +206,7 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad,
   uint8_t* sG_lo = smem + L.g_lo;
   float* sC = (float*)(smem + L.c_rows);
   float* sX = (float*)(smem + L.x_rows);
-  int16_t* sLk = (int16_t*)(smem + L.link_k);     // [j][LS]
+  uint16_t* sLk = (uint16_t*)(smem + L.link_k);   // [j][LS]
   int32_t* sLa = (int32_t*)(smem + L.link_a);     // [r][kpad]
   const float* cb = c + (int64_t)b * c_stride;
   const uint32_t tcols = tmem_cols_for(kpad);
@@ -237,16 +223,20 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad,
       dlo[i] = src[n16 + i];
     }
   }
-  for (int it = tid; it < R * nstr; it += TC_THREADS) {
-    const int r = it / nstr, k = it - r * nstr;
+  // rows a of c with one zero pad element each (row stride nstr + 1): the
+  // column-link encoding below points missing links at the pad
+  for (int it = tid; it < R * (nstr + 1); it += TC_THREADS) {
+    const int r = it / (nstr + 1), k = it - r * (nstr + 1);
     const int a = a0 + r;
-    sC[it] = a < nstr ? cb[a * nstr + k] : 0.f;
-    sX[it] = 0.f;
+    sC[it] = (a < nstr && k < nstr) ? cb[a * nstr + k] : 0.f;
   }
+  for (int it = tid; it < R * nstr; it += TC_THREADS) sX[it] = 0.f;
+  // row links as element offsets: 2 (J nstr) + negative, or -1
   for (int it = tid; it < R * kpad; it += TC_THREADS) {
     const int r = it / kpad, P = it - r * kpad;
     const int a = a0 + r;
-    sLa[it] = (a < nstr && P < npair) ? link[a * npair + P] : -1;
+    const int t = (a < nstr && P < npair) ? link[a * npair + P] : -1;
+    sLa[it] = t < 0 ? -1 : (((t >> 1) * nstr) << 1) | (t & 1);
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -274,7 +264,7 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad,
   const int gr = gm / W, gj = gm % W;            // W is a power of two
   const int ga = a0 + gr;
   const int32_t* la = sLa + gr * kpad;
-  const float* crow = sC + gr * nstr;
+  const float* crow = sC + gr * (nstr + 1);
   // epilogue mapping: warp w reads TMEM lanes 32 (w mod 4) + lane = m and
   // the 8-column chunks ch = w / 4, w / 4 + 2, ... of the pair columns
   const int em = 32 * (warp & 3) + lane;
@@ -282,31 +272,30 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad,
   float* xrow = sX + er * nstr;
 
   // link rows of the column strings of tile kt (contiguous in link) into
-  // buffer buf of sLk, one warp per row
+  // buffer buf of sLk, one warp per row, encoded as J | negative << 15 with a
+  // missing link (and every pair beyond npair or column beyond nstr) as the
+  // pad index nstr, so that the gather needs no branch
   auto stage_links = [&](int kt, int buf) {
     const int nc = min(W, nstr - kt);
-    int16_t* base = sLk + buf * W * LS;
+    uint16_t* base = sLk + buf * W * LS;
     for (int j = warp; j < W; j += TC_THREADS / 32) {
-      int16_t* dst = base + j * LS;
-      if (j < nc) {
-        const int32_t* src = link + (int64_t)(kt + j) * npair;
-        int32_t v[4];
+      uint16_t* dst = base + j * LS;
+      const int32_t* src = link + (int64_t)(kt + j) * npair;
+      int32_t v[4];
 #pragma unroll
-        for (int u = 0; u < 4; u++) v[u] = lane + 32 * u < npair ? src[lane + 32 * u] : -1;
+      for (int u = 0; u < 4; u++) v[u] = (j < nc && lane + 32 * u < npair) ? src[lane + 32 * u] : -1;
 #pragma unroll
-        for (int u = 0; u < 4; u++)
-          if (lane + 32 * u < kpad) dst[lane + 32 * u] = (int16_t)v[u];
-      } else {
-        for (int P = lane; P < kpad; P += 32) dst[P] = (int16_t)-1;
-      }
+      for (int u = 0; u < 4; u++)
+        if (lane + 32 * u < kpad)
+          dst[lane + 32 * u] =
+              (uint16_t)(v[u] < 0 ? nstr : ((v[u] >> 1) | ((v[u] & 1) << 15)));
     }
   };
   stage_links(0, 0);
   __syncthreads();
   int cur = 0;
   for (int k0 = 0; k0 < nstr && ok; k0 += W, cur ^= 1) {
-    const int ncol = min(W, nstr - k0);
-    const int16_t* lkg = sLk + cur * W * LS + gj * LS;
+    const uint16_t* lkg = sLk + cur * W * LS + gj * LS;
     // ---- gather D^T rows (determinant (a0 + r, k0 + j))
     {
       const int k = k0 + gj;
@@ -325,17 +314,13 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad,
 #pragma unroll
         for (int q = 0; q < 8; q++) {
           v[q] = 0.f;
-          if (col_ok) {
-            if (ta[q] >= 0) {
-              const float x = ccol[(ta[q] >> 1) * nstr];
-              v[q] = (ta[q] & 1) ? -x : x;
-            }
-            const int tk = (int)(int16_t)(kw[q >> 1] >> (16 * (q & 1)));
-            if (tk >= 0) {
-              const float x = crow[tk >> 1];
-              v[q] += (tk & 1) ? -x : x;
-            }
+          if (col_ok && ta[q] >= 0) {      // uniform over the warp (one row a)
+            const float x = ccol[ta[q] >> 1];
+            v[q] = (ta[q] & 1) ? -x : x;
           }
+          const uint32_t e = (kw[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
+          const float x = crow[e & 0x7FFFu];          // 0 at the pad
+          v[q] += (e & 0x8000u) ? -x : x;
         }
         // split into bf16 hi + lo, two values per conversion
         uint4 hv, lv;
@@ -383,21 +368,21 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad,
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     // ---- epilogue: E^T from TMEM, push 1/2 s E into the X row of m
+    // (rows a >= nstr accumulate zeros into an unused X row; columns beyond
+    // nstr carry the pad index and are skipped)
     if (ok) {
-      const bool m_ok = a0 + er < nstr && ej < ncol;
-      const int16_t* lke = sLk + cur * W * LS + ej * LS;
+      const uint16_t* lke = sLk + cur * W * LS + ej * LS;
 #pragma unroll 1
       for (int ch = warp >> 2; ch < nkb; ch += 2) {
         float e[8];
         tmem_ld8(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(ch * 8), e);
-        if (m_ok) {
-          const int4 kv = *reinterpret_cast<const int4*>(lke + ch * 8);
-          const uint32_t kw[4] = {(uint32_t)kv.x, (uint32_t)kv.y, (uint32_t)kv.z, (uint32_t)kv.w};
+        const int4 kv = *reinterpret_cast<const int4*>(lke + ch * 8);
+        const uint32_t kw[4] = {(uint32_t)kv.x, (uint32_t)kv.y, (uint32_t)kv.z, (uint32_t)kv.w};
 #pragma unroll
-          for (int q = 0; q < 8; q++) {
-            const int t = (int)(int16_t)(kw[q >> 1] >> (16 * (q & 1)));
-            if (t >= 0) atomicAdd(&xrow[t >> 1], (t & 1) ? -0.5f * e[q] : 0.5f * e[q]);
-          }
+        for (int q = 0; q < 8; q++) {
+          const uint32_t t = (kw[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
+          const uint32_t J = t & 0x7FFFu;
+          if (J != (uint32_t)nstr) atomicAdd(&xrow[J], (t & 0x8000u) ? -0.5f * e[q] : 0.5f * e[q]);
         }
       }
     }

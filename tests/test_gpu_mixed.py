@@ -153,3 +153,29 @@ def test_emulated_fp64_energies_vs_oracle(lib):
     for t, e in zip(tk, eps):
         assert abs(e - oc.casci(h, eri, w["nocc"], om.active_space(w["ref"], t))) < 1e-9
     m.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_warm_start_same_increments(lib, precision):
+    """Starting each tuple from its parent's converged vector (the tuple
+    less one orbital, previous order; opt-in) reaches the same increments as
+    the cold start, to the tolerance of the mode, on a system where the
+    parent states lead to the ground-state root."""
+    n, nocc = 12, 4
+    h, eri, _ = ms.gen_integrals(n, nocc, 41)
+    ref, exp = [2, 3, 4, 5], [0, 1, 6, 7, 8, 9, 10, 11]
+    prec = lib.MBE_FP64 if precision == "fp64" else lib.MBE_MIXED_BF16X3
+    tol = 1e-10 if precision == "fp64" else TOL_MIXED_INC
+    runs = {}
+    for warm in (0, 1):
+        m = lib.MBE(0, precision=prec, warm_start=warm)
+        m.load(h, eri, 2 * nocc)
+        lib.mbe_reset_stats(m.ctx)
+        res = m.run(ref, exp, 4, 0.0)
+        runs[warm] = (res, lib.mbe_get_stats(m.ctx)["iters_total"])
+        m.close()
+    (cold, it_cold), (hot, it_hot) = runs[0], runs[1]
+    for oc_, oh in zip(cold["orders"], hot["orders"]):
+        assert np.array_equal(oc_["tuples"], oh["tuples"])
+        assert np.max(np.abs(np.asarray(oc_["inc"]) - np.asarray(oh["inc"]))) < tol
+    assert abs(cold["total"] - hot["total"]) < tol
