@@ -40,7 +40,10 @@ DEFAULT_WORKLOAD = "h2o_dz_8e23o"
 # DRAM traffic per launch of the dominant kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by kernel; valid only
 # while the kernel source is unchanged (sha256 of the source file).
-TRAFFIC = {}
+# ncu capture (profiles/k_sigma_tc_8e12o_batch64.md): dram__bytes_read.sum +
+# dram__bytes_write.sum of one k_sigma_tc launch over 64 active 8e/12o
+# tuples (2 N_det npair^2 = 1.9081e+11 flop), per algorithmic flop
+TRAFFIC = {"k_sigma_tc": {"bytes_per_flop": 4.684638e-04, "sha": "37b08c47dee047ca"}}
 
 
 def peaks():
@@ -51,8 +54,17 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def src_sha(path):
-    return hashlib.sha256(open(os.path.join(ROOT, path), "rb").read()).hexdigest()[:16]
+def src_sha(path, kernel=None):
+    """sha256 prefix of a source file, or of one kernel's definition in it
+    (from its signature line to the first line that is a lone closing brace)."""
+    text = open(os.path.join(ROOT, path)).read()
+    if kernel:
+        lines = text.splitlines()
+        start = next(i for i, l in enumerate(lines) if l.startswith(kernel + "(")
+                     or (" " + kernel + "(") in l and "__global__" in l)
+        end = next(i for i in range(start, len(lines)) if lines[i] == "}")
+        text = "\n".join(lines[start:end + 1])
+    return hashlib.sha256(text.encode()).hexdigest()[:16]
 
 
 class ClockSampler:
@@ -322,8 +334,12 @@ def main():
         peak_src = f"bf16 dense sustained, {pk_kind}"
         bound = "tensor"
         ksrc = "paper_1905_02786_gb300/csrc/mbe_sigma_tc.cu"
+    # DRAM bytes per algorithmic flop from one ncu capture of the kernel
+    # (8e/12o batch of 64 tuples, bench --profile-batch 64), scaled to this
+    # run's average launch; null once the kernel source has changed
     tr = TRAFFIC.get(kname)
-    traffic = tr["bytes"] if tr and tr["sha"] == src_sha(ksrc) else None
+    traffic = (tr["bytes_per_flop"] * dom_flops_per
+               if tr and tr["sha"] == src_sha(ksrc, kname) else None)
     roofline = {"bound": bound, "kernel": kname, "achieved": achieved_tf, "peak": peak_tf,
                 "unit": "TFLOP/s", "frac": (achieved_tf / peak_tf) if achieved_tf else None,
                 "traffic": traffic, "peak_source": peak_src,
