@@ -731,10 +731,34 @@ int mbe_sigma(mbe_ctx* ctx, const int* act, int nact, const double* c, double* s
       if (e_core) *e_core = ec;
       return MBE_OK;
     } else {
-      const bool emu = ctx->opt.precision == MBE_EMULATED_FP64 && ozaki_supported(bp.npair);
-      sigma_fp64(ctx, bp, w, cd.ptr, bp.ndet, sd.ptr, bp.ndet, nullptr, ctx->opt.spin_shift, emu);
-      if (emu && sigma_tc_error(ctx, w))
-        return fail(ctx, MBE_ECUDA, "tensor-core contraction wait timed out");
+      // emulated FP64: the fused exact kernel for vectors like the mixed
+      // mode's exact points (c = c^T with FP32 values, |c_i| <= 1), else the
+      // sliced contraction on HBM intermediates
+      bool fused = ctx->opt.precision == MBE_EMULATED_FP64 &&
+                   sigma_exact_supported(bp.npair, bp.nstr);
+      for (int64_t i = 0; fused && i < bp.nstr; i++)
+        for (int64_t j = 0; j <= i; j++) {
+          const double x = c[i * bp.nstr + j];
+          if (x != c[j * bp.nstr + i] || (double)(float)x != x || std::fabs(x) > 1.0) {
+            fused = false;
+            break;
+          }
+        }
+      if (fused) {
+        std::vector<float> cf(c, c + bp.ndet);
+        DevBuf<float> cdf(&ctx->pool, bp.ndet);
+        CU_CHECK(cudaMemcpyAsync(cdf.ptr, cf.data(), sizeof(float) * bp.ndet, cudaMemcpyHostToDevice,
+                                 ctx->stream));
+        sigma_exact(ctx, bp, w, cdf.ptr, bp.ndet, sd.ptr, bp.ndet, nullptr);
+        launch_finish_sym_fp64(ctx, bp, sd.ptr, bp.ndet, cd.ptr, bp.ndet, ctx->opt.spin_shift,
+                               nullptr);
+        if (sigma_tc_error(ctx, w)) return fail(ctx, MBE_ECUDA, "fused exact sigma wait timed out");
+      } else {
+        const bool emu = ctx->opt.precision == MBE_EMULATED_FP64 && ozaki_supported(bp.npair);
+        sigma_fp64(ctx, bp, w, cd.ptr, bp.ndet, sd.ptr, bp.ndet, nullptr, ctx->opt.spin_shift, emu);
+        if (emu && sigma_tc_error(ctx, w))
+          return fail(ctx, MBE_ECUDA, "tensor-core contraction wait timed out");
+      }
     }
     CU_CHECK(cudaMemcpyAsync(sigma, sd.ptr, sizeof(double) * bp.ndet, cudaMemcpyDeviceToHost,
                              ctx->stream));

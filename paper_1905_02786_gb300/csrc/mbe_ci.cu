@@ -527,10 +527,12 @@ __global__ void k_finish_sym_fp64(double* __restrict__ out, int64_t out_stride,
       const int64_t idx = (int64_t)ia * nstr + ib;
       double v = sX[h][i][tx] + sX[1 - h][tx][i];
       if (shift != 0.0) {
-        const int32_t* la = link + (int64_t)ia * npair;
-        const int32_t* lb = link + (int64_t)ib * npair;
-        const uint32_t ma = masks[ia], mb = masks[ib];
-        double s2 = (double)(nsig - __popc(ma & mb)) * cb[idx];
+        // evaluated for (min, max): bitwise the same for both elements
+        const int lo = min(ia, ib), hi = max(ia, ib);
+        const int32_t* la = link + (int64_t)lo * npair;
+        const int32_t* lb = link + (int64_t)hi * npair;
+        const uint32_t ma = masks[lo], mb = masks[hi];
+        double s2 = (double)(nsig - __popc(ma & mb)) * cb[(int64_t)lo * nstr + hi];
         uint32_t oa = ma & ~mb;
         const uint32_t obm = mb & ~ma;
         while (oa) {
@@ -810,5 +812,15 @@ void convert_f64_to_f32(mbe_ctx* ctx, const double* src, float* dst, int64_t n) 
   if (n <= 0) return;
   k_f64_to_f32<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, ctx->stream>>>(
       src, dst, n);
+  CU_LAUNCH_CHECK();
+}
+
+void launch_finish_sym_fp64(mbe_ctx* ctx, const BinProblem& bp, double* out, int64_t out_stride,
+                            const double* c, int64_t c_stride, double spin_shift,
+                            const int32_t* active) {
+  const int ntl = (bp.nstr + 31) / 32;
+  k_finish_sym_fp64<<<dim3((unsigned)(ntl * (ntl + 1) / 2), bp.B), 256, 0, ctx->stream>>>(
+      out, out_stride, bp.tab->link.ptr, bp.tab->masks.ptr, bp.nstr, bp.n, bp.nsig, c, c_stride,
+      spin_shift, active);
   CU_LAUNCH_CHECK();
 }

@@ -398,6 +398,63 @@ __global__ void k32_save_yprev(const double* __restrict__ y, int m, int M, int r
         restarted ? (i == 0 ? 1.0 : 0.0) : (i < m ? y[(int64_t)b * M + i] : 0.0);
 }
 
+// Diagonal of H + shift S^2 in FP32 for the preconditioner (FP64 where it
+// accumulates over a string): e(I) = sum_{p in I} h_pp + 1/2 sum_{p,q in I}
+// (J_pq - K_pq) per string, then
+//   H_II = e(a) + e(b) + sum_{p in a, q in b} J_pq + shift (nsig - |a & b|)
+// with the alpha-beta Coulomb sum taken over pairs p >= q of a | b in a
+// fixed order, so that H(a,b) = H(b,a) bitwise.
+__global__ void k32_string_energy(const uint32_t* __restrict__ masks, int nstr, int n,
+                                  const double* __restrict__ heff_all,
+                                  const double* __restrict__ jk_all, float* __restrict__ estr) {
+  const int b = blockIdx.y;
+  const double* heff = heff_all + (int64_t)b * n * n;
+  const double* J = jk_all + (int64_t)b * 2 * n * n;
+  const double* K = J + n * n;
+  for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < nstr; I += gridDim.x * blockDim.x) {
+    const uint32_t m = masks[I];
+    double e = 0.0, e2 = 0.0;
+    for (uint32_t mp = m; mp; mp &= mp - 1) {
+      const int p = __ffs(mp) - 1;
+      e += heff[p * n + p];
+      for (uint32_t mq = m; mq; mq &= mq - 1) {
+        const int q = __ffs(mq) - 1;
+        e2 += J[p * n + q] - K[p * n + q];
+      }
+    }
+    estr[(int64_t)b * nstr + I] = (float)(e + 0.5 * e2);
+  }
+}
+
+__global__ void k32_hdiag(const uint32_t* __restrict__ masks, int nstr, int n, int nsig,
+                          const double* __restrict__ jk_all, const float* __restrict__ estr,
+                          float shift, float* __restrict__ hd_all) {
+  const int b = blockIdx.y;
+  __shared__ float sJ[MBE_MAX_ACT * MBE_MAX_ACT];
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x)
+    sJ[t] = (float)jk_all[(int64_t)b * 2 * n * n + t];
+  __syncthreads();
+  const int64_t N = (int64_t)nstr * nstr;
+  const float* eb = estr + (int64_t)b * nstr;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int ia = (int)(i / nstr), ib = (int)(i - (int64_t)ia * nstr);
+    const uint32_t ma = masks[ia], mb = masks[ib], mu = ma | mb;
+    float cross = 0.f;
+    for (uint32_t mp = mu; mp; mp &= mp - 1) {
+      const int p = __ffs(mp) - 1;
+      const int ap = (ma >> p) & 1, bp = (mb >> p) & 1;
+      for (uint32_t mq = mu & ((2u << p) - 1u); mq; mq &= mq - 1) {
+        const int q = __ffs(mq) - 1;
+        const int w = q == p ? (ap & bp) : ap * ((mb >> q) & 1) + ((ma >> q) & 1) * bp;
+        if (w) cross = fmaf((float)w, sJ[p * n + q], cross);
+      }
+    }
+    hd_all[(int64_t)b * N + i] =
+        (eb[ia] + eb[ib]) + cross + shift * (float)(nsig - __popc(ma & mb));
+  }
+}
+
 __global__ void k32_guess(const float* __restrict__ hd, int nstr, int M, float* __restrict__ V) {
   const int b = blockIdx.x;
   const int64_t N = (int64_t)nstr * nstr;
@@ -437,19 +494,16 @@ __global__ void k32_guess(const float* __restrict__ hd, int nstr, int M, float* 
   }
 }
 
-__global__ void k32_from_f64(const double* __restrict__ src, float* __restrict__ dst, int64_t n) {
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x)
-    dst[k] = (float)src[k];
-}
-
 // V0 = X / |X| (FP32) and its FP64 copy C64 (input of the exact sigma)
 __global__ void k32_exact_prep(const float* __restrict__ X, const double* __restrict__ xx,
                                float* __restrict__ V, int M, double* __restrict__ C64, int64_t N,
                                const int32_t* __restrict__ active) {
   const int b = blockIdx.y;
   if (!active[b]) return;
-  const float inv = (float)(1.0 / sqrt(xx[b]));
+  __shared__ float s_inv;
+  if (threadIdx.x == 0) s_inv = (float)(1.0 / sqrt(xx[b]));   // one FP64 root per block
+  __syncthreads();
+  const float inv = s_inv;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N;
        k += (int64_t)gridDim.x * blockDim.x) {
     const float v = X[(int64_t)b * N + k] * inv;
@@ -554,7 +608,7 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
   const int nchunks = (int)((N + CH - 1) / CH);
   DevBuf<float> V(P, (size_t)B * M * N), AV(P, (size_t)B * M * N), hd(P, (size_t)B * N),
       T(P, (size_t)B * N), X(P, (size_t)B * N), RX(P, (size_t)B * N);
-  DevBuf<double> hd64(P, (size_t)B * N), C64(P, (size_t)B * N), S64(P, (size_t)B * N),
+  DevBuf<double> C64(P, (size_t)B * N), S64(P, (size_t)B * N),
       G(P, (size_t)B * M * M), y(P, (size_t)B * M), yp(P, (size_t)B * M), theta(P, B),
       thx(P, B), rnorm(P, B), tolr(P, B), coef(P, (size_t)B * M), cdot(P, B), rdot(P, B),
       xx(P, B), xax(P, B), partial(P, (size_t)B * M * nchunks), rpart(P, (size_t)B * nchunks);
@@ -570,9 +624,15 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
   int64_t vecs_tc = 0, vecs_ex = 0;
 
   // diagonal (FP64 kernel shared with the FP64 mode), kept in FP32
-  launch_hdiag(ctx, bp, shift, hd64.ptr);
-  k32_from_f64<<<ge.x, 256, 0, st>>>(hd64.ptr, hd.ptr, (int64_t)B * N);
-  CU_LAUNCH_CHECK();
+  {
+    DevBuf<float> estr(P, (size_t)B * bp.nstr);
+    k32_string_energy<<<dim3((unsigned)((bp.nstr + 255) / 256), B), 256, 0, st>>>(
+        bp.tab->masks.ptr, bp.nstr, bp.n, bp.heff.ptr, bp.jk.ptr, estr.ptr);
+    CU_LAUNCH_CHECK();
+    k32_hdiag<<<ge, 256, 0, st>>>(bp.tab->masks.ptr, bp.nstr, bp.n, bp.nsig, bp.jk.ptr, estr.ptr,
+                                  (float)shift, hd.ptr);
+    CU_LAUNCH_CHECK();
+  }
   k32_guess<<<B, 256, 0, st>>>(hd.ptr, bp.nstr, M, V.ptr);
   CU_LAUNCH_CHECK();
   if (plan) launch_parent_guess(ctx, *plan, bp.n, bp.nsig, bp.nstr, V.ptr, nullptr, (int64_t)M * N);
@@ -675,6 +735,8 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
       m++;
     }
   };
+  // the exact-point sigma: fused on the tensor cores where it fits (kpad <= 80)
+  const bool exact_fused = sigma_exact_supported(bp.npair, bp.nstr);
   // exact point of the tuples in `mask`: V0 = x/|x|, exact A V0, theta_x,
   // r_x and its norm; G = [[V0.AV0]]
   auto exact_point = [&]() {
@@ -684,7 +746,12 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
     k32_exact_prep<<<ge, 256, 0, st>>>(X.ptr, xx.ptr, V.ptr, M, C64.ptr, N, active.ptr);
     CU_LAUNCH_CHECK();
     dot_comp(V.ptr, (int64_t)M * N, V.ptr, (int64_t)M * N, xx.ptr, active.ptr);
-    sigma_fp64(ctx, bp, sw, C64.ptr, N, S64.ptr, N, active.ptr, shift, true, true);
+    if (exact_fused) {
+      sigma_exact(ctx, bp, sw, V.ptr, (int64_t)M * N, S64.ptr, N, active.ptr);
+      launch_finish_sym_fp64(ctx, bp, S64.ptr, N, C64.ptr, N, shift, active.ptr);
+    } else {
+      sigma_fp64(ctx, bp, sw, C64.ptr, N, S64.ptr, N, active.ptr, shift, true, true);
+    }
     vecs_ex += B;
     k32_exact_xax<<<gc, RT, 0, st>>>(C64.ptr, S64.ptr, N, nchunks, active.ptr, rpart.ptr);
     CU_LAUNCH_CHECK();

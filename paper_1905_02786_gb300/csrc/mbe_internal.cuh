@@ -261,6 +261,8 @@ struct SigmaWork {
   DevBuf<double> D, E;           // scratch for the FP64 path
   DevBuf<float> Xf;              // X rows of the tensor-core path (sigma = X + X^T)
   DevBuf<int32_t> err;           // timeout flag of the tensor-core path
+  DevBuf<uint8_t> gex;           // g' digit planes of the fused exact sigma
+  DevBuf<int32_t> gexp;          // their row exponents
   int64_t sub_batch = 0;
 };
 bool sigma_tc_supported(int n, int nstr);
@@ -284,6 +286,16 @@ void sigma_fp64(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const double* c,
                 const int32_t* active, double spin_shift, bool emulated,
                 bool symmetric = false);
 bool ozaki_supported(int npair);
+// FP64-grade sigma of FP32 vectors c (c = c^T, |c_i| <= 1) fused on the
+// tensor cores: writes the rows X (sigma = X + X^T + shift S^2 c follows in
+// launch_finish_sym_fp64)
+bool sigma_exact_supported(int npair, int nstr);
+void sigma_exact(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const float* c, int64_t c_stride,
+                 double* X, int64_t x_stride, const int32_t* active);
+// out = X + X^T + shift S^2 c in place for every tuple of the batch (c = c^T)
+void launch_finish_sym_fp64(mbe_ctx* ctx, const BinProblem& bp, double* out, int64_t out_stride,
+                            const double* c, int64_t c_stride, double spin_shift,
+                            const int32_t* active);
 void contract_ozaki(mbe_ctx* ctx, const double* gp, int npair, const double* D, int64_t ndet,
                     int nb, const int32_t* active, const int32_t* bmap, double* E,
                     int32_t* err);

@@ -179,3 +179,33 @@ def test_warm_start_same_increments(lib, precision):
         assert np.array_equal(oc_["tuples"], oh["tuples"])
         assert np.max(np.abs(np.asarray(oc_["inc"]) - np.asarray(oh["inc"]))) < tol
     assert abs(cold["total"] - hot["total"]) < tol
+
+
+@pytest.mark.parametrize("case", [
+    (8, 3, 1, [0, 1, 2, 3, 4, 5]),
+    (14, 4, 2, list(range(12))),                    # 8e/12o, npair 78 (kpad 80)
+    (10, 4, 5, [1, 3, 4, 5, 7, 8, 9]),              # inactive core + deleted virtuals
+    (12, 4, 0, [0, 1, 2, 3, 4, 5, 6, 7, 8]),        # ragged tiles
+])
+def test_sigma_exact_fused_elementwise(lib, case):
+    """The fused exact-point sigma (gather, exact 8-bit digits of D and g',
+    grouped exact FP32 accumulators in tensor memory, 64-bit fixed-point
+    scatter) for symmetric vectors with FP32 values, as at the exact points
+    of the mixed mode: element by element to 1e-9 of the largest element,
+    and exactly symmetric."""
+    norb, nocc, seed, act = case
+    h, eri, _ = ms.gen_integrals(norb, nocc, seed)
+    sp = oc.Space(h, eri, nocc, act)
+    m = lib.MBE(0, precision=lib.MBE_EMULATED_FP64, spin_shift=0.5)
+    m.load(h, eri, 2 * nocc)
+    c = ms.random_symmetric_ci(sp.nstr, seed + 7)[0]
+    c = (c / np.linalg.norm(c)).astype(np.float32).astype(np.float64)
+    sig, ecore = lib.mbe_sigma(m.ctx, act, c)
+    S = core_signs(sp, nocc, act)
+    cs = S * c.ravel()
+    ref = S * (sp.sigma(cs) + 0.5 * sp.s2(cs) - ecore * cs)
+    scale = np.abs(ref).max()
+    assert np.abs(sig - ref).max() <= 1e-9 * scale
+    s2 = sig.reshape(sp.nstr, sp.nstr)
+    assert np.array_equal(s2, s2.T)
+    m.close()
