@@ -58,6 +58,12 @@ void DevPool::trim() {
   free_blocks.clear();
 }
 
+int64_t DevPool::cached() const {
+  int64_t t = 0;
+  for (const auto& kv : free_blocks) t += (int64_t)kv.first;
+  return t;
+}
+
 DevPool::~DevPool() {
   cudaDeviceSynchronize();
   for (auto& kv : sizes) cudaFree(kv.first);
@@ -158,14 +164,21 @@ void solve_jobs(mbe_ctx* ctx, const std::vector<std::vector<int>>& acts, double*
   if (ci_out) ci_out->assign(acts.size(), {});
   size_t free_b = 0, total_b = 0;
   CU_CHECK(cudaMemGetInfo(&free_b, &total_b));
-  double budget = std::min(0.5 * (double)free_b, 96e9);
+  // the pool's cached free blocks are reusable: they count as free
+  double budget = std::min(0.5 * ((double)free_b + (double)ctx->pool.cached()), 96e9);
   if (ctx->opt.mem_cap_bytes > 0) budget = std::min(budget, 0.5 * (double)ctx->opt.mem_cap_bytes);
   const int M = std::max(4, std::min(32, ctx->opt.max_subspace));
   for (auto& kv : bins) {
     const int n = kv.first.first, nsig = kv.first.second;
     StringTables* tab = get_tables(ctx, n, nsig);
     const int64_t N = (int64_t)tab->nstr * tab->nstr;
-    double per = (double)(2 * M + 6) * N * 8.0 + (double)tab->npair * tab->npair * 8.0;
+    // device bytes per tuple: the mixed Davidson holds V and AV (M vectors
+    // each) and four work vectors in FP32 plus two FP64 exact-point vectors;
+    // the FP64 one 2M + 6 FP64 vectors
+    const bool mixed_bin = ctx->opt.precision == MBE_MIXED_BF16X3 && N > 1 &&
+                           sigma_tc_supported(n, tab->nstr) && ozaki_supported(tab->npair);
+    double per = (mixed_bin ? (double)(8 * M + 32) * N : (double)(2 * M + 6) * N * 8.0) +
+                 (double)tab->npair * tab->npair * 8.0 * 2.0;
     int64_t bmem = std::max<int64_t>(1, (int64_t)(budget / per));
     int64_t bmax = std::min<int64_t>(std::max(1, ctx->opt.max_batch), bmem);
     const std::vector<int64_t>& idx = kv.second;

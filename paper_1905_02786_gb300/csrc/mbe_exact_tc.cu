@@ -246,14 +246,13 @@ k_sigma_exact(const int32_t* __restrict__ link, int nstr, int npair, int kpad,
     const int4 kv = *reinterpret_cast<const int4*>(lkg + pb);
     const int ta[8] = {a0v.x, a0v.y, a0v.z, a0v.w, a1v.x, a1v.y, a1v.z, a1v.w};
     const uint32_t kw[4] = {(uint32_t)kv.x, (uint32_t)kv.y, (uint32_t)kv.z, (uint32_t)kv.w};
-    const float* ccol = cb + k;
+    const float* ccol = cb + (col_ok ? k : 0);   // column 0 stands in for an invalid one
+    float xa[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) xa[q] = ccol[ta[q] >= 0 ? (ta[q] >> 1) : 0];
 #pragma unroll
     for (int q = 0; q < 8; q++) {
-      d1[q] = 0.f;
-      if (col_ok && ta[q] >= 0) {
-        const float x = ccol[ta[q] >> 1];
-        d1[q] = (ta[q] & 1) ? -x : x;
-      }
+      d1[q] = (col_ok && ta[q] >= 0) ? ((ta[q] & 1) ? -xa[q] : xa[q]) : 0.f;
       const uint32_t e = (kw[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
       const float x = crow[e & 0x7FFFu];
       d2[q] = (e & 0x8000u) ? -x : x;

@@ -75,6 +75,7 @@ struct DevPool {
   void* alloc(size_t bytes);
   void release(void* p);
   void trim();
+  int64_t cached() const;   // bytes held in free blocks (reusable)
   ~DevPool();
 };
 

@@ -108,15 +108,18 @@ __global__ void k_split_gp(const double* __restrict__ gp_all, int npair, int kpa
 // One CTA = tuple b (blockIdx.y) x rows [a0, a0 + R) of X (blockIdx.x).  An
 // MMA tile is M = 128 determinants m = r W + j <-> (a0 + r, k0 + j), r < R,
 // j < W = 128 / R; the accumulator holds E^T (lane m, column P), computed
-// as D^T g' (g' is symmetric) with N = kpad pair columns.
-template <int R>
+// as D^T g' (g' is symmetric) with N = kpad pair columns.  kpad (the pair
+// count rounded up to 16) is a template parameter: loop trip counts, the
+// operand layout and the link stride are compile-time constants.
+template <int R, int KP>
 __global__ void __launch_bounds__(TC_THREADS, 2)
-k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad,
+k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair,
            const uint8_t* __restrict__ gsplit, const float* __restrict__ c, int64_t c_stride,
            const int32_t* __restrict__ active, float* __restrict__ X, int64_t x_stride,
            int32_t* __restrict__ err) {
   constexpr int W = TC_N / R;
-  const int LS = link_stride(kpad);
+  constexpr int kpad = KP;
+  constexpr int LS = 8 * ((KP >> 3) | 1);     // link_stride(kpad)
   const int b = blockIdx.y;
   if (active && !active[b]) return;
   const int a0 = blockIdx.x * R;
@@ -177,9 +180,9 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad,
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base_sh;
-  const uint32_t idesc = make_idesc(TC_M, kpad);
-  const uint32_t sbo = (uint32_t)(kpad >> 3) * 128u;
-  const int nkb = kpad >> 3;
+  constexpr uint32_t idesc = make_idesc(TC_M, kpad);
+  constexpr uint32_t sbo = (uint32_t)(kpad >> 3) * 128u;
+  constexpr int nkb = kpad >> 3;
   uint32_t phase = 0;
   bool ok = true;
 
@@ -225,7 +228,9 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad,
     {
       const int k = k0 + gj;
       const bool col_ok = ga < nstr && k < nstr;
-      const float* ccol = cb + k;                 // column k of c, row stride nstr
+      // column k of c (row stride nstr); column 0 stands in for an invalid
+      // determinant so that the loads below need no branch
+      const float* ccol = cb + (col_ok ? k : 0);
       for (int kb = tid >> 7; kb < nkb; kb += 2) {
         const int pb = kb * 8;
         // 8 pairs at once: two 16-byte loads of the row link, one of the
@@ -235,14 +240,15 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair, int kpad,
         const int4 kv = *reinterpret_cast<const int4*>(lkg + pb);
         const int ta[8] = {a0v.x, a0v.y, a0v.z, a0v.w, a1v.x, a1v.y, a1v.z, a1v.w};
         const uint32_t kw[4] = {(uint32_t)kv.x, (uint32_t)kv.y, (uint32_t)kv.z, (uint32_t)kv.w};
+        // the eight row-link loads are issued together (a missing link reads
+        // row 0 and is discarded), then combined
+        float xa[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) xa[q] = ccol[ta[q] >= 0 ? (ta[q] >> 1) : 0];
         float v[8];
 #pragma unroll
         for (int q = 0; q < 8; q++) {
-          v[q] = 0.f;
-          if (col_ok && ta[q] >= 0) {      // uniform over the warp (one row a)
-            const float x = ccol[ta[q] >> 1];
-            v[q] = (ta[q] & 1) ? -x : x;
-          }
+          v[q] = (col_ok && ta[q] >= 0) ? ((ta[q] & 1) ? -xa[q] : xa[q]) : 0.f;
           const uint32_t e = (kw[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
           const float x = crow[e & 0x7FFFu];          // 0 at the pad
           v[q] += (e & 0x8000u) ? -x : x;
@@ -381,6 +387,57 @@ __global__ void k_sigma_tc_finish(const float* __restrict__ X, int64_t x_stride,
   }
 }
 
+// one instantiation per (rows per CTA, padded pair count)
+template <int R, int KP>
+void launch_tc_kp(int device, dim3 grid, uint32_t smem, cudaStream_t st, const int32_t* link,
+                  int nstr, int npair, const uint8_t* gsplit, const float* c, int64_t c_stride,
+                  const int32_t* active, float* X, int64_t x_stride, int32_t* err) {
+  static bool attr_done[64] = {false};
+  if (!attr_done[device]) {
+    CU_CHECK(cudaFuncSetAttribute(k_sigma_tc<R, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  227 * 1024 - 1024));
+    attr_done[device] = true;
+  }
+  k_sigma_tc<R, KP><<<grid, TC_THREADS, smem, st>>>(link, nstr, npair, gsplit, c, c_stride,
+                                                    active, X, x_stride, err);
+}
+
+template <int R>
+void launch_tc_r(int device, int kpad, dim3 grid, uint32_t smem, cudaStream_t st,
+                 const int32_t* link, int nstr, int npair, const uint8_t* gsplit, const float* c,
+                 int64_t c_stride, const int32_t* active, float* X, int64_t x_stride,
+                 int32_t* err) {
+  switch (kpad) {
+#define MBE_TC_CASE(KP)                                                                    \
+  case KP:                                                                                 \
+    launch_tc_kp<R, KP>(device, grid, smem, st, link, nstr, npair, gsplit, c, c_stride,   \
+                        active, X, x_stride, err);                                         \
+    break;
+    MBE_TC_CASE(16)
+    MBE_TC_CASE(32)
+    MBE_TC_CASE(48)
+    MBE_TC_CASE(64)
+    MBE_TC_CASE(80)
+    MBE_TC_CASE(96)
+    MBE_TC_CASE(112)
+    MBE_TC_CASE(128)
+#undef MBE_TC_CASE
+    default:
+      throw MbeError{MBE_EINVAL, "unsupported pair padding for the tensor-core sigma"};
+  }
+}
+
+void launch_tc(int device, int R, int kpad, dim3 grid, uint32_t smem, cudaStream_t st,
+               const int32_t* link, int nstr, int npair, const uint8_t* gsplit, const float* c,
+               int64_t c_stride, const int32_t* active, float* X, int64_t x_stride, int32_t* err) {
+  if (R == 2)
+    launch_tc_r<2>(device, kpad, grid, smem, st, link, nstr, npair, gsplit, c, c_stride, active,
+                   X, x_stride, err);
+  else
+    launch_tc_r<1>(device, kpad, grid, smem, st, link, nstr, npair, gsplit, c, c_stride, active,
+                   X, x_stride, err);
+}
+
 }  // namespace
 
 bool sigma_tc_supported(int n, int nstr) {
@@ -410,26 +467,12 @@ void sigma_tc(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const float* c, int64_
     k_split_gp<<<dim3(8, bp.B), 256, 0, ctx->stream>>>(bp.gp.ptr, npair, kpad, bp.gsplit.ptr);
     CU_LAUNCH_CHECK();
   }
-  static int attr_done[64] = {0};
-  if (!attr_done[ctx->device]) {
-    CU_CHECK(cudaFuncSetAttribute(k_sigma_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  227 * 1024 - 1024));
-    CU_CHECK(cudaFuncSetAttribute(k_sigma_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  227 * 1024 - 1024));
-    attr_done[ctx->device] = 1;
-  }
   CU_CHECK(cudaMemsetAsync(w.err.ptr, 0, sizeof(int32_t), ctx->stream));
   dim3 grid((unsigned)((nstr + R - 1) / R), bp.B);
   cudaEvent_t ev;
   ctx->dom_timer.begin(ctx->stream, ctx->opt.timing != 0, &ev);
-  if (R == 2)
-    k_sigma_tc<2><<<grid, TC_THREADS, L.total, ctx->stream>>>(bp.tab->link.ptr, nstr, npair, kpad,
-                                                               bp.gsplit.ptr, c, c_stride, active,
-                                                               w.Xf.ptr, N, w.err.ptr);
-  else
-    k_sigma_tc<1><<<grid, TC_THREADS, L.total, ctx->stream>>>(bp.tab->link.ptr, nstr, npair, kpad,
-                                                               bp.gsplit.ptr, c, c_stride, active,
-                                                               w.Xf.ptr, N, w.err.ptr);
+  launch_tc(ctx->device, R, kpad, grid, L.total, ctx->stream, bp.tab->link.ptr, nstr, npair,
+            bp.gsplit.ptr, c, c_stride, active, w.Xf.ptr, N, w.err.ptr);
   CU_LAUNCH_CHECK();
   ctx->dom_timer.end(ctx->stream, ev);
   ctx->stats.dom_launches += 1;
