@@ -66,7 +66,7 @@ __host__ __device__ inline TcShared tc_layout(int kpad, int R, int nstr, int npa
   s.c_rows = take((uint32_t)R * (nstr + 1) * 4);
   s.x_rows = take((uint32_t)R * nstr * 4);
   s.link_k = take((uint32_t)2 * W * link_stride(kpad) * 2);
-  s.link_a = take((uint32_t)R * kpad * 4);
+  s.link_a = take((uint32_t)R * kpad * 8);      // offsets, then signs
   s.total = o;
   return s;
 }
@@ -135,7 +135,8 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair,
   float* sC = (float*)(smem + L.c_rows);
   float* sX = (float*)(smem + L.x_rows);
   uint16_t* sLk = (uint16_t*)(smem + L.link_k);   // [j][LS]
-  int32_t* sLa = (int32_t*)(smem + L.link_a);     // [r][kpad]
+  int32_t* sLa = (int32_t*)(smem + L.link_a);     // [r][kpad] element offsets J nstr
+  float* sLm = (float*)(sLa + R * kpad);           // [r][kpad] sign, 0 without a link
   const float* cb = c + (int64_t)b * c_stride;
   const uint32_t tcols = tmem_cols_for(kpad);
 
@@ -159,12 +160,14 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair,
     sC[it] = (a < nstr && k < nstr) ? cb[a * nstr + k] : 0.f;
   }
   for (int it = tid; it < R * nstr; it += TC_THREADS) sX[it] = 0.f;
-  // row links as element offsets: 2 (J nstr) + negative, or -1
+  // row links as an element offset J nstr and a sign (0 where there is no
+  // link: the load then reads column k of row 0 and is multiplied away)
   for (int it = tid; it < R * kpad; it += TC_THREADS) {
     const int r = it / kpad, P = it - r * kpad;
     const int a = a0 + r;
     const int t = (a < nstr && P < npair) ? link[a * npair + P] : -1;
-    sLa[it] = t < 0 ? -1 : (((t >> 1) * nstr) << 1) | (t & 1);
+    sLa[it] = t < 0 ? 0 : (t >> 1) * nstr;
+    sLm[it] = t < 0 ? 0.f : ((t & 1) ? -1.f : 1.f);
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -192,12 +195,14 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair,
   const int gr = gm / W, gj = gm % W;            // W is a power of two
   const int ga = a0 + gr;
   const int32_t* la = sLa + gr * kpad;
+  const float* lm = sLm + gr * kpad;
   const float* crow = sC + gr * (nstr + 1);
   // epilogue mapping: warp w reads TMEM lanes 32 (w mod 4) + lane = m and
   // the 8-column chunks ch = w / 4, w / 4 + 2, ... of the pair columns
   const int em = 32 * (warp & 3) + lane;
   const int er = em / W, ej = em % W;
   float* xrow = sX + er * nstr;
+  const uint32_t xrow_s = smem_u32(xrow);
 
   // link rows of the column strings of tile kt (contiguous in link) into
   // buffer buf of sLk, one warp per row, encoded as J | negative << 15 with a
@@ -240,18 +245,21 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair,
         const int4 kv = *reinterpret_cast<const int4*>(lkg + pb);
         const int ta[8] = {a0v.x, a0v.y, a0v.z, a0v.w, a1v.x, a1v.y, a1v.z, a1v.w};
         const uint32_t kw[4] = {(uint32_t)kv.x, (uint32_t)kv.y, (uint32_t)kv.z, (uint32_t)kv.w};
-        // the eight row-link loads are issued together (a missing link reads
-        // row 0 and is discarded), then combined
+        const float4 m0v = *reinterpret_cast<const float4*>(lm + pb);
+        const float4 m1v = *reinterpret_cast<const float4*>(lm + pb + 4);
+        const float sa[8] = {m0v.x, m0v.y, m0v.z, m0v.w, m1v.x, m1v.y, m1v.z, m1v.w};
+        // the eight row-link loads are issued together, then combined; the
+        // D rows of determinants beyond nstr are never scattered, so they
+        // need no masking (their loads stay in bounds through ccol)
         float xa[8];
 #pragma unroll
-        for (int q = 0; q < 8; q++) xa[q] = ccol[ta[q] >= 0 ? (ta[q] >> 1) : 0];
+        for (int q = 0; q < 8; q++) xa[q] = ccol[ta[q]];
         float v[8];
 #pragma unroll
         for (int q = 0; q < 8; q++) {
-          v[q] = (col_ok && ta[q] >= 0) ? ((ta[q] & 1) ? -xa[q] : xa[q]) : 0.f;
           const uint32_t e = (kw[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
           const float x = crow[e & 0x7FFFu];          // 0 at the pad
-          v[q] += (e & 0x8000u) ? -x : x;
+          v[q] = fmaf(sa[q], xa[q], __int_as_float(__float_as_int(x) ^ ((e & 0x8000u) << 16)));
         }
         // split into bf16 hi + lo, two values per conversion
         uint4 hv, lv;
@@ -313,7 +321,13 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair,
         for (int q = 0; q < 8; q++) {
           const uint32_t t = (kw[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
           const uint32_t J = t & 0x7FFFu;
-          if (J != (uint32_t)nstr) atomicAdd(&xrow[J], (t & 0x8000u) ? -0.5f * e[q] : 0.5f * e[q]);
+          const float val = __int_as_float(__float_as_int(0.5f * e[q]) ^ ((t & 0x8000u) << 16));
+          // predicated shared-memory reduction (no branch): skipped at the pad
+          asm volatile(
+              "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, %3;\n\t"
+              "@p red.shared.add.f32 [%0], %1;\n\t}\n" ::"r"(xrow_s + 4u * J),
+              "f"(val), "r"(J), "r"((uint32_t)nstr)
+              : "memory");
         }
       }
     }
@@ -387,6 +401,10 @@ __global__ void k_sigma_tc_finish(const float* __restrict__ X, int64_t x_stride,
   }
 }
 
+// rows of X per CTA: a tile of 128 determinants spans W = 128 / R column
+// strings, so more rows mean fewer column-link rows staged per tile
+inline int tc_rows(int nstr) { return nstr <= 1024 ? 4 : (nstr <= 2048 ? 2 : 1); }
+
 // one instantiation per (rows per CTA, padded pair count)
 template <int R, int KP>
 void launch_tc_kp(int device, dim3 grid, uint32_t smem, cudaStream_t st, const int32_t* link,
@@ -430,7 +448,10 @@ void launch_tc_r(int device, int kpad, dim3 grid, uint32_t smem, cudaStream_t st
 void launch_tc(int device, int R, int kpad, dim3 grid, uint32_t smem, cudaStream_t st,
                const int32_t* link, int nstr, int npair, const uint8_t* gsplit, const float* c,
                int64_t c_stride, const int32_t* active, float* X, int64_t x_stride, int32_t* err) {
-  if (R == 2)
+  if (R == 4)
+    launch_tc_r<4>(device, kpad, grid, smem, st, link, nstr, npair, gsplit, c, c_stride, active,
+                   X, x_stride, err);
+  else if (R == 2)
     launch_tc_r<2>(device, kpad, grid, smem, st, link, nstr, npair, gsplit, c, c_stride, active,
                    X, x_stride, err);
   else
@@ -444,7 +465,7 @@ bool sigma_tc_supported(int n, int nstr) {
   const int npair = n * (n + 1) / 2;
   if (npair > TC_M) return false;
   const int kpad = ((npair + 15) / 16) * 16;
-  const int R = nstr <= 2048 ? 2 : 1;
+  const int R = tc_rows(nstr);
   TcShared L = tc_layout(kpad, R, nstr, npair, TC_N / R);
   return L.total + 2048 <= 227 * 1024;
 }
@@ -453,7 +474,7 @@ void sigma_tc(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const float* c, int64_
               float* out, int64_t out_stride, const int32_t* active, double spin_shift) {
   const int npair = bp.npair, nstr = bp.nstr;
   const int kpad = ((npair + 15) / 16) * 16;
-  const int R = nstr <= 2048 ? 2 : 1;
+  const int R = tc_rows(nstr);
   const TcShared L = tc_layout(kpad, R, nstr, npair, TC_N / R);
   if (L.total + 2048 > 227 * 1024 || npair > TC_M)
     throw MbeError{MBE_EINVAL, "active space too large for the tensor-core sigma"};
