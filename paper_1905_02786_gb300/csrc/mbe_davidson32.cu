@@ -149,47 +149,6 @@ __global__ void k32_jacobi(const double* __restrict__ G, int m, int M,
   ritz_lowest(G + (int64_t)b * M * M, m, M, S, theta + b, y + (int64_t)b * M);
 }
 
-// x = V y; r = AV y - theta x (stage A), or with exact0
-// r = y_0 (r_x + (theta_x - theta) V_0) + sum_{i>=1} y_i (AV_i - theta V_i)
-__global__ void k32_residual(const float* __restrict__ V, const float* __restrict__ AV,
-                             const float* __restrict__ RX, int exact0, int m, int M, int64_t N,
-                             const double* __restrict__ y, const double* __restrict__ theta,
-                             const double* __restrict__ thx, const int32_t* __restrict__ active,
-                             float* __restrict__ X, float* __restrict__ T, int nchunks,
-                             double* __restrict__ partial) {
-  const int b = blockIdx.y;
-  if (!active[b]) return;
-  __shared__ float sy[32];
-  __shared__ double red[32];
-  if (threadIdx.x < m) sy[threadIdx.x] = (float)y[(int64_t)b * M + threadIdx.x];
-  __syncthreads();
-  const float th = (float)theta[b];
-  const float dth = exact0 ? (float)(thx[b] - theta[b]) : 0.f;
-  const int64_t k0 = (int64_t)blockIdx.x * CH, k1 = min(N, k0 + CH);
-  const float* Vb = V + (int64_t)b * M * N;
-  const float* AVb = AV + (int64_t)b * M * N;
-  float acc = 0.f;
-  for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
-    float x = 0.f, r = 0.f;
-    const int i0 = exact0 ? 1 : 0;
-    if (exact0) {
-      const float v0 = Vb[k];
-      x = sy[0] * v0;
-      r = sy[0] * (RX[(int64_t)b * N + k] + dth * v0);
-    }
-    for (int i = i0; i < m; i++) {
-      const float v = Vb[(int64_t)i * N + k];
-      x = fmaf(sy[i], v, x);
-      r = fmaf(sy[i], AVb[(int64_t)i * N + k] - th * v, r);
-    }
-    X[(int64_t)b * N + k] = x;
-    T[(int64_t)b * N + k] = r;
-    acc = fmaf(r, r, acc);
-  }
-  const double tot = block_sum((double)acc, red);
-  if (threadIdx.x == 0) partial[(int64_t)b * nchunks + blockIdx.x] = tot;
-}
-
 __global__ void k32_converge(const double* __restrict__ partial, int nchunks, int B, int it,
                              const double* __restrict__ tol_r, int rel,
                              const double* __restrict__ theta, double* __restrict__ rnorm,
@@ -260,23 +219,6 @@ __global__ void k32_precondition(float* __restrict__ T, const float* __restrict_
   }
 }
 
-__global__ void k32_orth_axpy(float* __restrict__ T, const float* __restrict__ V, int m, int M,
-                              int64_t N, const double* __restrict__ coef,
-                              const int32_t* __restrict__ active) {
-  const int b = blockIdx.y;
-  if (!active[b]) return;
-  __shared__ float sc[32];
-  if (threadIdx.x < m) sc[threadIdx.x] = (float)coef[(int64_t)b * M + threadIdx.x];
-  __syncthreads();
-  const float* Vb = V + (int64_t)b * M * N;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    float t = T[(int64_t)b * N + k];
-    for (int i = 0; i < m; i++) t = fmaf(-sc[i], Vb[(int64_t)i * N + k], t);
-    T[(int64_t)b * N + k] = t;
-  }
-}
-
 __global__ void k32_append(const float* __restrict__ T, float* __restrict__ V, int m, int M,
                            int64_t N, const double* __restrict__ nrm2,
                            int32_t* __restrict__ active) {
@@ -295,6 +237,125 @@ __global__ void k32_append(const float* __restrict__ T, float* __restrict__ V, i
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N;
        k += (int64_t)gridDim.x * blockDim.x)
     V[(int64_t)b * M * N + (int64_t)m * N + k] = T[(int64_t)b * N + k] * inv;
+}
+
+// Per-thread FP32 dot accumulators of the fused kernels below live in shared
+// memory, sD[i][thread] (registers stay few and occupancy high: these kernels
+// are bound by HBM).  Block sums of sD[i][.] for i < m, in FP64, go to
+// partial[(b m + i) nchunks + chunk] (the layout of k32_multidot).
+__device__ __forceinline__ void sd_sums_to_partial(const float (*sD)[RT], int m,
+                                                   double* __restrict__ partial, int b,
+                                                   int chunk, int nchunks) {
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = warp; i < m; i += RT / 32) {
+    double v = 0.0;
+#pragma unroll
+    for (int j = 0; j < RT / 32; j++) v += (double)sD[i][lane + 32 * j];
+    for (int off = 16; off; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) partial[((int64_t)b * m + i) * nchunks + chunk] = v;
+  }
+}
+
+// The residual step with the preconditioner and the first orthogonalisation
+// pass's dot products folded in:
+//   x = V y,  r = AV y - theta x (stage A), or with exact0
+//   r = y_0 (r_x + (theta_x - theta) V_0) + sum_{i>=1} y_i (AV_i - theta V_i),
+//   |r|^2 partials,
+//   t = r / (theta - H_II)  (every vector is alpha-beta symmetric bitwise, so
+//       this equals the symmetrised form of k32_precondition),
+//   partials of V_i . t, i < m.
+// The second read of V_i[k] follows the first within the same thread and is
+// served by the caches, so V streams from HBM once instead of twice.
+__global__ void __launch_bounds__(RT) k32_residual_pre(
+    const float* __restrict__ V, const float* __restrict__ AV, const float* __restrict__ RX,
+    int exact0, int m, int M, int64_t N, const double* __restrict__ y,
+    const double* __restrict__ theta, const double* __restrict__ thx,
+    const float* __restrict__ hd, const int32_t* __restrict__ active, float* __restrict__ X,
+    float* __restrict__ T, int nchunks, double* __restrict__ rpart,
+    double* __restrict__ dpart) {
+  const int b = blockIdx.y;
+  if (!active[b]) return;
+  __shared__ float sy[32];
+  __shared__ float sD[32][RT];
+  __shared__ double red[32];
+  if (threadIdx.x < m) sy[threadIdx.x] = (float)y[(int64_t)b * M + threadIdx.x];
+  for (int i = 0; i < m; i++) sD[i][threadIdx.x] = 0.f;
+  __syncthreads();
+  const float th = (float)theta[b];
+  const float dth = exact0 ? (float)(thx[b] - theta[b]) : 0.f;
+  const int i0 = exact0 ? 1 : 0;
+  const int64_t k0 = (int64_t)blockIdx.x * CH, k1 = min(N, k0 + CH);
+  const float* Vb = V + (int64_t)b * M * N;
+  const float* AVb = AV + (int64_t)b * M * N;
+  const float* hb = hd + (int64_t)b * N;
+  float acc = 0.f;
+  for (int64_t k = k0 + threadIdx.x; k < k1; k += RT) {
+    float x = 0.f, r = 0.f;
+    if (exact0) {
+      const float v0 = Vb[k];
+      x = sy[0] * v0;
+      r = sy[0] * (RX[(int64_t)b * N + k] + dth * v0);
+    }
+    for (int i = i0; i < m; i++) {
+      const float v = Vb[(int64_t)i * N + k];
+      x = fmaf(sy[i], v, x);
+      r = fmaf(sy[i], AVb[(int64_t)i * N + k] - th * v, r);
+    }
+    X[(int64_t)b * N + k] = x;
+    acc = fmaf(r, r, acc);
+    float d = th - hb[k];
+    if (fabsf(d) < 1e-4f) d = d < 0.f ? -1e-4f : 1e-4f;
+    const float t = r / d;
+    T[(int64_t)b * N + k] = t;
+    for (int i = 0; i < m; i++)
+      sD[i][threadIdx.x] = fmaf(Vb[(int64_t)i * N + k], t, sD[i][threadIdx.x]);
+  }
+  const double tot = block_sum((double)acc, red);
+  if (threadIdx.x == 0) rpart[(int64_t)b * nchunks + blockIdx.x] = tot;
+  sd_sums_to_partial(sD, m, dpart, b, blockIdx.x, nchunks);
+}
+
+// One classical Gram-Schmidt update T <- T - sum_{i<m} c_i V_i, with the dot
+// products the next step needs taken in the same pass (V_i[k] read twice by
+// one thread, the second time from the caches):
+//   norm == 0: partials of V_i . T (the second pass's coefficients),
+//   norm == 1: partials of T . T (the normalisation).
+__global__ void __launch_bounds__(RT) k32_orth_pass(float* __restrict__ T,
+                                                   const float* __restrict__ V, int m, int M,
+                                                   int64_t N, const double* __restrict__ coef,
+                                                   const int32_t* __restrict__ active, int norm,
+                                                   int nchunks, double* __restrict__ partial) {
+  const int b = blockIdx.y;
+  if (!active[b]) return;
+  __shared__ float sc[32];
+  __shared__ float sD[32][RT];
+  __shared__ double red[32];
+  if (threadIdx.x < m) sc[threadIdx.x] = (float)coef[(int64_t)b * M + threadIdx.x];
+  if (!norm)
+    for (int i = 0; i < m; i++) sD[i][threadIdx.x] = 0.f;
+  __syncthreads();
+  const int64_t k0 = (int64_t)blockIdx.x * CH, k1 = min(N, k0 + CH);
+  const float* Vb = V + (int64_t)b * M * N;
+  float* Tb = T + (int64_t)b * N;
+  float nacc = 0.f;
+  for (int64_t k = k0 + threadIdx.x; k < k1; k += RT) {
+    float t = Tb[k];
+    for (int i = 0; i < m; i++) t = fmaf(-sc[i], Vb[(int64_t)i * N + k], t);
+    Tb[k] = t;
+    if (norm) {
+      nacc = fmaf(t, t, nacc);
+    } else {
+      for (int i = 0; i < m; i++)
+        sD[i][threadIdx.x] = fmaf(Vb[(int64_t)i * N + k], t, sD[i][threadIdx.x]);
+    }
+  }
+  if (norm) {
+    const double tot = block_sum((double)nacc, red);
+    if (threadIdx.x == 0) partial[(int64_t)b * nchunks + blockIdx.x] = tot;
+  } else {
+    sd_sums_to_partial(sD, m, partial, b, blockIdx.x, nchunks);
+  }
 }
 
 __global__ void k32_fix_frozen(int32_t* active, int B) {
@@ -673,16 +734,29 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
     }
     return n;
   };
-  // precondition T, orthogonalise against V[0..m) twice, append as V[m]
-  auto extend = [&](int m) {
-    k32_precondition<<<gpre, 256, 0, st>>>(T.ptr, hd.ptr, bp.nstr, theta.ptr, active.ptr);
-    CU_LAUNCH_CHECK();
-    for (int pass = 0; pass < 2; pass++) {
-      dots(V.ptr, (int64_t)M * N, N, T.ptr, N, m, coef.ptr, M, 1, active.ptr);
-      k32_orth_axpy<<<ge, 256, 0, st>>>(T.ptr, V.ptr, m, M, N, coef.ptr, active.ptr);
+  // orthogonalise T against V[0..m) twice (classical Gram-Schmidt), append
+  // as V[m].  raw: T is an unpreconditioned residual; dots_ready: T is
+  // preconditioned and `partial` holds the first pass's V_i . T partials
+  // (both from k32_residual_pre)
+  auto extend = [&](int m, bool raw, bool dots_ready) {
+    if (raw) {
+      k32_precondition<<<gpre, 256, 0, st>>>(T.ptr, hd.ptr, bp.nstr, theta.ptr, active.ptr);
       CU_LAUNCH_CHECK();
     }
-    dots(T.ptr, N, 0, T.ptr, N, 1, coef.ptr, M, 1, active.ptr);
+    if (dots_ready) {
+      k32_final<<<B, 32, 0, st>>>(partial.ptr, m, nchunks, active.ptr, coef.ptr, M, 1);
+      CU_LAUNCH_CHECK();
+    } else {
+      dots(V.ptr, (int64_t)M * N, N, T.ptr, N, m, coef.ptr, M, 1, active.ptr);
+    }
+    for (int pass = 0; pass < 2; pass++) {
+      k32_orth_pass<<<gc, RT, 0, st>>>(T.ptr, V.ptr, m, M, N, coef.ptr, active.ptr, pass,
+                                      nchunks, partial.ptr);
+      CU_LAUNCH_CHECK();
+      k32_final<<<B, 32, 0, st>>>(partial.ptr, pass ? 1 : m, nchunks, active.ptr, coef.ptr, M,
+                                  1);
+      CU_LAUNCH_CHECK();
+    }
     k32_append<<<ge, 256, 0, st>>>(T.ptr, V.ptr, m, M, N, coef.ptr, active.ptr);
     CU_LAUNCH_CHECK();
     k32_fix_frozen<<<1, 256, 0, st>>>(active.ptr, B);
@@ -710,9 +784,9 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
       CU_LAUNCH_CHECK();
       k32_jacobi<<<B, 32, 0, st>>>(G.ptr, m, M, active.ptr, theta.ptr, y.ptr);
       CU_LAUNCH_CHECK();
-      k32_residual<<<gc, RT, 0, st>>>(V.ptr, AV.ptr, RX.ptr, exact0 ? 1 : 0, m, M, N, y.ptr,
-                                      theta.ptr, thx.ptr, active.ptr, X.ptr, T.ptr, nchunks,
-                                      rpart.ptr);
+      k32_residual_pre<<<gc, RT, 0, st>>>(V.ptr, AV.ptr, RX.ptr, exact0 ? 1 : 0, m, M, N,
+                                          y.ptr, theta.ptr, thx.ptr, hd.ptr, active.ptr, X.ptr,
+                                          T.ptr, nchunks, rpart.ptr, partial.ptr);
       CU_LAUNCH_CHECK();
       k32_converge<<<1, 256, 0, st>>>(rpart.ptr, nchunks, B, m_start > 1 ? it + 1 : it, tolr.ptr,
                                       rel, theta.ptr, rnorm.ptr, active.ptr, iters.ptr, nact.ptr);
@@ -731,7 +805,8 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
       }
       k32_save_yprev<<<B, 32, 0, st>>>(y.ptr, m, M, restarted, active.ptr, yp.ptr);
       CU_LAUNCH_CHECK();
-      extend(m);
+      // after a restart V changed: the first pass's dots are taken again
+      extend(m, false, !restarted);
       m++;
     }
   };
@@ -803,7 +878,7 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
     CU_CHECK(cudaMemcpyAsync(T.ptr, RX.ptr, sizeof(float) * B * N, cudaMemcpyDeviceToDevice, st));
     k32_save_yprev<<<B, 32, 0, st>>>(y.ptr, 1, M, 1, active.ptr, yp.ptr);
     CU_LAUNCH_CHECK();
-    extend(1);
+    extend(1, true, false);
     stage(2, 40, 0, true, na);
   }
   if (sigma_tc_error(ctx, sw)) throw MbeError{MBE_ECUDA, "tensor-core sigma wait timed out"};
