@@ -260,9 +260,22 @@ def main():
     allgather = driver.torch_allgather() if world > 1 else None
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
+    order_s = []
+
     def step():
+        # host-side seconds per order (the solve returns its energies to the
+        # host, so each order ends synchronised): a breakdown, not the metric
+        order_s.clear()
+        t_last = [time.perf_counter()]
+
+        def mark(rec):
+            t = time.perf_counter()
+            order_s.append({"order": rec["order"], "tuples": len(rec["tuples"]),
+                            "s": round(t - t_last[0], 4)})
+            t_last[0] = t
+
         return driver.run_expansion(m.ctx, w["ref"], w["exp"], max_order, w["thr"], rank, world,
-                                    allgather)
+                                    allgather, callback=mark)
 
     def barrier():
         if world > 1:
@@ -413,6 +426,7 @@ def main():
                     "fp64_vectors_per_casci": st["fp64_flops"] / max(st["sigma_flops"], 1)
                     * st["sigma_vectors"] / max(st["casci"], 1)},
                 "davidson_iters_mean": st["iters_total"] / max(st["casci"], 1),
+                "seconds_per_order": list(order_s),
                 "noconv": st["noconv"],
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "mixed_vs_fp64_gpu": cmp,

@@ -77,9 +77,10 @@ __host__ __device__ inline uint32_t tmem_cols_for(int kpad) {
   return c;
 }
 
-// Split of g' into bf16 hi + lo in the K-major core-matrix layout, once per
+// Split of g'/2 into bf16 hi + lo in the K-major core-matrix layout, once per
 // tuple (the sigma kernel copies its first kpad rows into shared memory):
 // gsplit[b] = {hi[128 x kpad], lo[128 x kpad]}, rows >= npair and K >= npair 0.
+// The factor 1/2 of sigma = X + X^T is carried here (exact: a power of two).
 __global__ void k_split_gp(const double* __restrict__ gp_all, int npair, int kpad,
                            uint8_t* __restrict__ gsplit) {
   const int b = blockIdx.y;
@@ -94,7 +95,7 @@ __global__ void k_split_gp(const double* __restrict__ gp_all, int npair, int kpa
 #pragma unroll
     for (int j = 0; j < 8; j++) {
       const int k = kb + j;
-      const double dv = (row < npair && k < npair) ? g[(int64_t)row * npair + k] : 0.0;
+      const double dv = (row < npair && k < npair) ? 0.5 * g[(int64_t)row * npair + k] : 0.0;
       const __nv_bfloat16 hh = __double2bfloat16(dv);
       h8[j] = hh;
       l8[j] = __double2bfloat16(dv - (double)__bfloat162float(hh));
@@ -236,30 +237,51 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair,
       // column k of c (row stride nstr); column 0 stands in for an invalid
       // determinant so that the loads below need no branch
       const float* ccol = cb + (col_ok ? k : 0);
-      for (int kb = tid >> 7; kb < nkb; kb += 2) {
-        const int pb = kb * 8;
-        // 8 pairs at once: two 16-byte loads of the row link, one of the
-        // column link (entries beyond npair are -1)
+      // nkb is even (kpad is a multiple of 16): nkb / 2 blocks of 8 pairs per
+      // thread.  Software pipelined: the eight row-link loads (from L2) of
+      // block jb + 1 are issued before block jb is combined and stored, so
+      // that their latency overlaps the arithmetic (a missing link has
+      // offset 0 and sign 0; D rows of determinants beyond nstr are never
+      // scattered, so they need no masking, and their loads stay in bounds
+      // through ccol)
+      float xa[8];
+      {
+        const int pb = (tid >> 7) * 8;
         const int4 a0v = *reinterpret_cast<const int4*>(la + pb);
         const int4 a1v = *reinterpret_cast<const int4*>(la + pb + 4);
-        const int4 kv = *reinterpret_cast<const int4*>(lkg + pb);
         const int ta[8] = {a0v.x, a0v.y, a0v.z, a0v.w, a1v.x, a1v.y, a1v.z, a1v.w};
+#pragma unroll
+        for (int q = 0; q < 8; q++) xa[q] = ccol[ta[q]];
+      }
+#pragma unroll
+      for (int jb = 0; jb < nkb / 2; jb++) {
+        const int kb = (tid >> 7) + 2 * jb;
+        const int pb = kb * 8;
+        float xn[8];
+        if (jb + 1 < nkb / 2) {
+          const int4 a0v = *reinterpret_cast<const int4*>(la + pb + 16);
+          const int4 a1v = *reinterpret_cast<const int4*>(la + pb + 20);
+          const int tn[8] = {a0v.x, a0v.y, a0v.z, a0v.w, a1v.x, a1v.y, a1v.z, a1v.w};
+#pragma unroll
+          for (int q = 0; q < 8; q++) xn[q] = ccol[tn[q]];
+        }
+        // 8 pairs at once: one 16-byte load of the column link, two of the
+        // row-link signs
+        const int4 kv = *reinterpret_cast<const int4*>(lkg + pb);
         const uint32_t kw[4] = {(uint32_t)kv.x, (uint32_t)kv.y, (uint32_t)kv.z, (uint32_t)kv.w};
         const float4 m0v = *reinterpret_cast<const float4*>(lm + pb);
         const float4 m1v = *reinterpret_cast<const float4*>(lm + pb + 4);
         const float sa[8] = {m0v.x, m0v.y, m0v.z, m0v.w, m1v.x, m1v.y, m1v.z, m1v.w};
-        // the eight row-link loads are issued together, then combined; the
-        // D rows of determinants beyond nstr are never scattered, so they
-        // need no masking (their loads stay in bounds through ccol)
-        float xa[8];
-#pragma unroll
-        for (int q = 0; q < 8; q++) xa[q] = ccol[ta[q]];
         float v[8];
 #pragma unroll
         for (int q = 0; q < 8; q++) {
           const uint32_t e = (kw[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
           const float x = crow[e & 0x7FFFu];          // 0 at the pad
           v[q] = fmaf(sa[q], xa[q], __int_as_float(__float_as_int(x) ^ ((e & 0x8000u) << 16)));
+        }
+        if (jb + 1 < nkb / 2) {
+#pragma unroll
+          for (int q = 0; q < 8; q++) xa[q] = xn[q];
         }
         // split into bf16 hi + lo, two values per conversion
         uint4 hv, lv;
@@ -306,28 +328,40 @@ k_sigma_tc(const int32_t* __restrict__ link, int nstr, int npair,
     }
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // ---- epilogue: E^T from TMEM, push 1/2 s E into the X row of m
+    // ---- epilogue: E^T from TMEM (g' carries the 1/2), push s E into the X row of m
     // (rows a >= nstr accumulate zeros into an unused X row; columns beyond
     // nstr carry the pad index and are skipped)
     if (ok) {
       const uint16_t* lke = sLk + cur * W * LS + ej * LS;
-#pragma unroll 1
-      for (int ch = warp >> 2; ch < nkb; ch += 2) {
-        float e[8];
-        tmem_ld8(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(ch * 8), e);
-        const int4 kv = *reinterpret_cast<const int4*>(lke + ch * 8);
-        const uint32_t kw[4] = {(uint32_t)kv.x, (uint32_t)kv.y, (uint32_t)kv.z, (uint32_t)kv.w};
+      const uint32_t tl = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+      // chunks ch = warp / 4 + 2 j, j < nkb / 2, two TMEM loads per wait
 #pragma unroll
-        for (int q = 0; q < 8; q++) {
-          const uint32_t t = (kw[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
-          const uint32_t J = t & 0x7FFFu;
-          const float val = __int_as_float(__float_as_int(0.5f * e[q]) ^ ((t & 0x8000u) << 16));
-          // predicated shared-memory reduction (no branch): skipped at the pad
-          asm volatile(
-              "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, %3;\n\t"
-              "@p red.shared.add.f32 [%0], %1;\n\t}\n" ::"r"(xrow_s + 4u * J),
-              "f"(val), "r"(J), "r"((uint32_t)nstr)
-              : "memory");
+      for (int j = 0; j < nkb / 2; j += 2) {
+        const int ch0 = (warp >> 2) + 2 * j;
+        const bool two = j + 1 < nkb / 2;
+        float e[16];
+        if (two)
+          tmem_ld8x2(tl + (uint32_t)(ch0 * 8), tl + (uint32_t)(ch0 * 8 + 16), e);
+        else
+          tmem_ld8(tl + (uint32_t)(ch0 * 8), e);
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+          if (h == 1 && !two) break;
+          const int ch = ch0 + 2 * h;
+          const int4 kv = *reinterpret_cast<const int4*>(lke + ch * 8);
+          const uint32_t kw[4] = {(uint32_t)kv.x, (uint32_t)kv.y, (uint32_t)kv.z, (uint32_t)kv.w};
+#pragma unroll
+          for (int q = 0; q < 8; q++) {
+            const uint32_t t = (kw[q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
+            const uint32_t J = t & 0x7FFFu;
+            const float val = __int_as_float(__float_as_int(e[8 * h + q]) ^ ((t & 0x8000u) << 16));
+            // predicated shared-memory reduction (no branch): skipped at the pad
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, %3;\n\t"
+                "@p red.shared.add.f32 [%0], %1;\n\t}\n" ::"r"(xrow_s + 4u * J),
+                "f"(val), "r"(J), "r"((uint32_t)nstr)
+                : "memory");
+          }
         }
       }
     }
