@@ -43,7 +43,7 @@ DEFAULT_WORKLOAD = "h2o_dz_8e23o"
 # ncu capture (profiles/k_sigma_tc_8e12o_batch64.md): dram__bytes_read.sum +
 # dram__bytes_write.sum of one k_sigma_tc launch over 64 active 8e/12o
 # tuples (2 N_det npair^2 = 1.9081e+11 flop), per algorithmic flop
-TRAFFIC = {"k_sigma_tc": {"bytes_per_flop": 4.671611e-04, "sha": "e88b14b2d83ac563"}}
+TRAFFIC = {"k_sigma_tc": {"bytes_per_flop": 4.666351e-04, "sha": "c5facf0329642a90"}}
 
 
 def peaks():

@@ -102,6 +102,16 @@ typedef struct mbe_options {
                            ground state, so the iteration can settle on the
                            wrong root; measured on the 8e/23o workload it
                            saved few iterations.                             */
+  /* Mixed-precision Davidson (MBE_MIXED_BF16X3) convergence schedule:       */
+  double mixed_stage_tol;  /* the tensor-core stage stops at this residual
+                              times max(1, |theta|) (default 1e-5)           */
+  double mixed_round_drop; /* each refinement round asks for its starting
+                              exact residual times this (0 < x < 1, default
+                              1e-2; the round stops earlier at the target)   */
+  double mixed_rel_tol;    /* final target max(conv_tol_r, this times
+                              max(1, |theta|)) on the exact residual (default
+                              2e-7: above the floor that FP32 storage of the
+                              CI vector sets, a few 1e-8 |H|)                */
 } mbe_options;
 
 typedef struct mbe_ctx mbe_ctx;
@@ -126,9 +136,10 @@ typedef struct mbe_stats {
   double fp64_flops;      /* their algorithmic flops                          */
 } mbe_stats;
 
-/* Fill *opt with the defaults (FP64, max_batch 256, subspace 16, 200
+/* Fill *opt with the defaults (FP64, max_batch 256, subspace 20, 400
  * iterations, tol_r 1e-8, tol_e 1e-12, spin_shift 0.5, keep_ci 0,
- * deterministic 1, no memory cap, warm_start 0). */
+ * deterministic 1, no memory cap, warm_start 0, mixed schedule 1e-5 / 1e-2 /
+ * 2e-7). */
 void mbe_default_options(mbe_options* opt);
 
 /* Create a context on CUDA device `device`.  opt may be NULL (defaults).

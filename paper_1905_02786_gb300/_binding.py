@@ -41,7 +41,9 @@ class mbe_options(ctypes.Structure):
                 ("spin_shift", ctypes.c_double), ("keep_ci", ctypes.c_int),
                 ("deterministic", ctypes.c_int), ("mem_cap_bytes", ctypes.c_int64),
                 ("timing", ctypes.c_int), ("verbose", ctypes.c_int),
-                ("backward_share", ctypes.c_int), ("warm_start", ctypes.c_int)]
+                ("backward_share", ctypes.c_int), ("warm_start", ctypes.c_int),
+                ("mixed_stage_tol", ctypes.c_double), ("mixed_round_drop", ctypes.c_double),
+                ("mixed_rel_tol", ctypes.c_double)]
 
 
 _lib = None
@@ -92,9 +94,14 @@ def _check(ctx, rc, allow=()):
     return rc
 
 
-def mbe_default_options() -> mbe_options:
+def mbe_default_options(**overrides) -> mbe_options:
+    """The library's defaults, with the named fields replaced."""
     o = mbe_options()
     load_library().mbe_default_options(ctypes.byref(o))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
     return o
 
 

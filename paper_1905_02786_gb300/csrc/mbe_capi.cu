@@ -292,6 +292,9 @@ void mbe_default_options(mbe_options* o) {
   o->verbose = 0;
   o->backward_share = 0;
   o->warm_start = 0;
+  o->mixed_stage_tol = 1e-5;
+  o->mixed_round_drop = 1e-2;
+  o->mixed_rel_tol = 2e-7;
 }
 
 int mbe_create(mbe_ctx** out, int device, const mbe_options* opt) {
@@ -304,6 +307,9 @@ int mbe_create(mbe_ctx** out, int device, const mbe_options* opt) {
       o.precision != MBE_EMULATED_FP64)
     return MBE_EINVAL;
   if (o.max_batch < 1 || o.max_subspace < 4 || o.max_subspace > 32 || o.max_iter < 1)
+    return MBE_EINVAL;
+  if (!(o.mixed_stage_tol > 0.0) || !(o.mixed_round_drop > 0.0 && o.mixed_round_drop < 1.0) ||
+      !(o.mixed_rel_tol > 0.0))
     return MBE_EINVAL;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {

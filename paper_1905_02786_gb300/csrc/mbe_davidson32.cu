@@ -13,11 +13,13 @@
 //   r_x    = A x - theta x, its norm in FP64.
 // Iteration (Davidson, J. Comput. Phys. 17, 87 (1975)):
 //   stage A: tensor-core (split-BF16x3) sigma vectors until the residual is
-//            below 1e-3 max(1, |theta|) (above their precision floor);
+//            below mixed_stage_tol max(1, |theta|) (default 1e-5, above
+//            their precision floor);
 //   rounds:  exact point; tuples with |r_x| above the target continue from
 //            {x, t_1, ...} where t_j get tensor-core sigma vectors and the
 //            couplings x.A t_j = theta (x.t_j) + r_x.t_j use only exact data;
-//            the stage stops at max(target, |r_x| / 100).
+//            the stage stops at max(target, mixed_round_drop |r_x|)
+//            (default |r_x| / 100).
 // The energy error of the reported Rayleigh quotient is below |r_x|^2 / gap.
 #include "mbe_internal.cuh"
 #include "mbe_ritz.cuh"
@@ -631,7 +633,7 @@ __global__ void k32_exact_fin(const double* __restrict__ xax, const double* __re
 // storage of x puts a floor of a few 1e-8 |A| on its exact residual
 __global__ void k32_select(const double* __restrict__ rnorm, const int32_t* __restrict__ mask,
                            const double* __restrict__ thx, int B, double abs_target,
-                           double rel_target, int32_t* __restrict__ active,
+                           double rel_target, double drop, int32_t* __restrict__ active,
                            double* __restrict__ tolr, int32_t* __restrict__ nactive) {
   __shared__ int cnt;
   if (threadIdx.x == 0) cnt = 0;
@@ -640,7 +642,7 @@ __global__ void k32_select(const double* __restrict__ rnorm, const int32_t* __re
     const double target = fmax(abs_target, rel_target * fmax(1.0, fabs(thx[b])));
     const int a = (mask[b] && rnorm[b] > target) ? 1 : 0;
     active[b] = a;
-    tolr[b] = fmax(target, 0.01 * rnorm[b]);
+    tolr[b] = fmax(target, drop * rnorm[b]);
     if (a) atomicAdd(&cnt, 1);
   }
   __syncthreads();
@@ -701,7 +703,7 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
   CU_LAUNCH_CHECK();
   CU_CHECK(cudaMemsetAsync(iters.ptr, 0, sizeof(int32_t) * B, st));
   CU_CHECK(cudaMemsetAsync(G.ptr, 0, sizeof(double) * B * M * M, st));
-  k32_fill_d<<<1, 256, 0, st>>>(tolr.ptr, B, 1e-3);
+  k32_fill_d<<<1, 256, 0, st>>>(tolr.ptr, B, ctx->opt.mixed_stage_tol);
   CU_LAUNCH_CHECK();
 
   auto dots = [&](const float* Xv, int64_t xb, int64_t xv, const float* Yv, int64_t yb, int m,
@@ -847,7 +849,7 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
   // stage A
   stage(1, 150, 1, false, B);
   // refinement rounds
-  const double abs_target = ctx->opt.conv_tol_r, rel_target = 2e-7;
+  const double abs_target = ctx->opt.conv_tol_r, rel_target = ctx->opt.mixed_rel_tol;
   k32_fill_i<<<1, 256, 0, st>>>(mask.ptr, B, 1);
   CU_LAUNCH_CHECK();
   std::vector<double> rn2(B);
@@ -862,7 +864,7 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
       if (mk[b]) rn2[b] = std::sqrt(std::max(0.0, rn2[b]));
     CU_CHECK(cudaMemcpyAsync(rnorm.ptr, rn2.data(), sizeof(double) * B, cudaMemcpyHostToDevice, st));
     k32_select<<<1, 256, 0, st>>>(rnorm.ptr, mask.ptr, thx.ptr, B, abs_target, rel_target,
-                                  active.ptr, tolr.ptr, nact.ptr);
+                                  ctx->opt.mixed_round_drop, active.ptr, tolr.ptr, nact.ptr);
     CU_LAUNCH_CHECK();
     const int na = count_active();
     if (ctx->opt.verbose) {
