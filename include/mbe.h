@@ -112,6 +112,13 @@ typedef struct mbe_options {
                               max(1, |theta|)) on the exact residual (default
                               2e-7: above the floor that FP32 storage of the
                               CI vector sets, a few 1e-8 |H|)                */
+  int pspace;              /* mixed mode: size of the P-space preconditioner,
+                              the number of alpha-beta symmetric basis
+                              functions of lowest diagonal energy whose block
+                              of H + lambda S^2 is solved exactly in the
+                              Davidson correction (0 = diagonal only; at most
+                              128; capped at half the symmetric space;
+                              default 128)                                   */
 } mbe_options;
 
 typedef struct mbe_ctx mbe_ctx;
@@ -139,7 +146,7 @@ typedef struct mbe_stats {
 /* Fill *opt with the defaults (FP64, max_batch 256, subspace 20, 400
  * iterations, tol_r 1e-8, tol_e 1e-12, spin_shift 0.5, keep_ci 0,
  * deterministic 1, no memory cap, warm_start 0, mixed schedule 1e-5 / 1e-2 /
- * 2e-7). */
+ * 2e-7, pspace 128). */
 void mbe_default_options(mbe_options* opt);
 
 /* Create a context on CUDA device `device`.  opt may be NULL (defaults).

@@ -43,7 +43,7 @@ class mbe_options(ctypes.Structure):
                 ("timing", ctypes.c_int), ("verbose", ctypes.c_int),
                 ("backward_share", ctypes.c_int), ("warm_start", ctypes.c_int),
                 ("mixed_stage_tol", ctypes.c_double), ("mixed_round_drop", ctypes.c_double),
-                ("mixed_rel_tol", ctypes.c_double)]
+                ("mixed_rel_tol", ctypes.c_double), ("pspace", ctypes.c_int)]
 
 
 _lib = None

@@ -173,11 +173,12 @@ void solve_jobs(mbe_ctx* ctx, const std::vector<std::vector<int>>& acts, double*
     StringTables* tab = get_tables(ctx, n, nsig);
     const int64_t N = (int64_t)tab->nstr * tab->nstr;
     // device bytes per tuple: the mixed Davidson holds V and AV (M vectors
-    // each) and four work vectors in FP32 plus two FP64 exact-point vectors;
-    // the FP64 one 2M + 6 FP64 vectors
+    // each) and five work vectors in FP32 plus two FP64 exact-point vectors
+    // and the P-space eigenvectors; the FP64 one 2M + 6 FP64 vectors
     const bool mixed_bin = ctx->opt.precision == MBE_MIXED_BF16X3 && N > 1 &&
                            sigma_tc_supported(n, tab->nstr) && ozaki_supported(tab->npair);
-    double per = (mixed_bin ? (double)(8 * M + 32) * N : (double)(2 * M + 6) * N * 8.0) +
+    double per = (mixed_bin ? (double)(8 * M + 36) * N + 128.0 * 129.0 * 4.0
+                            : (double)(2 * M + 6) * N * 8.0) +
                  (double)tab->npair * tab->npair * 8.0 * 2.0;
     int64_t bmem = std::max<int64_t>(1, (int64_t)(budget / per));
     int64_t bmax = std::min<int64_t>(std::max(1, ctx->opt.max_batch), bmem);
@@ -295,6 +296,7 @@ void mbe_default_options(mbe_options* o) {
   o->mixed_stage_tol = 1e-5;
   o->mixed_round_drop = 1e-2;
   o->mixed_rel_tol = 2e-7;
+  o->pspace = 128;
 }
 
 int mbe_create(mbe_ctx** out, int device, const mbe_options* opt) {
@@ -309,7 +311,7 @@ int mbe_create(mbe_ctx** out, int device, const mbe_options* opt) {
   if (o.max_batch < 1 || o.max_subspace < 4 || o.max_subspace > 32 || o.max_iter < 1)
     return MBE_EINVAL;
   if (!(o.mixed_stage_tol > 0.0) || !(o.mixed_round_drop > 0.0 && o.mixed_round_drop < 1.0) ||
-      !(o.mixed_rel_tol > 0.0))
+      !(o.mixed_rel_tol > 0.0) || o.pspace < 0 || o.pspace > 128)
     return MBE_EINVAL;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {

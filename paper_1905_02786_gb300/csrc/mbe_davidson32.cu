@@ -275,14 +275,21 @@ __global__ void __launch_bounds__(RT) k32_residual_pre(
     const double* __restrict__ theta, const double* __restrict__ thx,
     const float* __restrict__ hd, const int32_t* __restrict__ active, float* __restrict__ X,
     float* __restrict__ T, int nchunks, double* __restrict__ rpart,
-    double* __restrict__ dpart) {
+    double* __restrict__ dpart, int olsen, float* __restrict__ Uo,
+    double* __restrict__ upart, double* __restrict__ xpart) {
   const int b = blockIdx.y;
   if (!active[b]) return;
+  // per-thread dot accumulators: sD[i] for V_i . t, with olsen sE[i] for V_i . u
+  extern __shared__ float sdyn[];
+  float (*sD)[RT] = reinterpret_cast<float (*)[RT]>(sdyn);
+  float (*sE)[RT] = reinterpret_cast<float (*)[RT]>(sdyn + m * RT);
   __shared__ float sy[32];
-  __shared__ float sD[32][RT];
   __shared__ double red[32];
   if (threadIdx.x < m) sy[threadIdx.x] = (float)y[(int64_t)b * M + threadIdx.x];
-  for (int i = 0; i < m; i++) sD[i][threadIdx.x] = 0.f;
+  for (int i = 0; i < m; i++) {
+    sD[i][threadIdx.x] = 0.f;
+    if (olsen) sE[i][threadIdx.x] = 0.f;
+  }
   __syncthreads();
   const float th = (float)theta[b];
   const float dth = exact0 ? (float)(thx[b] - theta[b]) : 0.f;
@@ -291,7 +298,7 @@ __global__ void __launch_bounds__(RT) k32_residual_pre(
   const float* Vb = V + (int64_t)b * M * N;
   const float* AVb = AV + (int64_t)b * M * N;
   const float* hb = hd + (int64_t)b * N;
-  float acc = 0.f;
+  float acc = 0.f, xt = 0.f, xu = 0.f;
   for (int64_t k = k0 + threadIdx.x; k < k1; k += RT) {
     float x = 0.f, r = 0.f;
     if (exact0) {
@@ -310,12 +317,64 @@ __global__ void __launch_bounds__(RT) k32_residual_pre(
     if (fabsf(d) < 1e-4f) d = d < 0.f ? -1e-4f : 1e-4f;
     const float t = r / d;
     T[(int64_t)b * N + k] = t;
-    for (int i = 0; i < m; i++)
-      sD[i][threadIdx.x] = fmaf(Vb[(int64_t)i * N + k], t, sD[i][threadIdx.x]);
+    if (olsen) {
+      const float u = x / d;
+      Uo[(int64_t)b * N + k] = u;
+      xt = fmaf(x, t, xt);
+      xu = fmaf(x, u, xu);
+      for (int i = 0; i < m; i++) {
+        const float v = Vb[(int64_t)i * N + k];
+        sD[i][threadIdx.x] = fmaf(v, t, sD[i][threadIdx.x]);
+        sE[i][threadIdx.x] = fmaf(v, u, sE[i][threadIdx.x]);
+      }
+    } else {
+      for (int i = 0; i < m; i++)
+        sD[i][threadIdx.x] = fmaf(Vb[(int64_t)i * N + k], t, sD[i][threadIdx.x]);
+    }
   }
   const double tot = block_sum((double)acc, red);
   if (threadIdx.x == 0) rpart[(int64_t)b * nchunks + blockIdx.x] = tot;
+  if (olsen) {
+    __syncthreads();
+    const double s_xt = block_sum((double)xt, red);
+    if (threadIdx.x == 0) xpart[((int64_t)b * 2) * nchunks + blockIdx.x] = s_xt;
+    __syncthreads();
+    const double s_xu = block_sum((double)xu, red);
+    if (threadIdx.x == 0) xpart[((int64_t)b * 2 + 1) * nchunks + blockIdx.x] = s_xu;
+    sd_sums_to_partial(sE, m, upart, b, blockIdx.x, nchunks);
+  }
   sd_sums_to_partial(sD, m, dpart, b, blockIdx.x, nchunks);
+}
+
+// Olsen's correction with the P-space preconditioner M = theta - A_0:
+// t = M^-1 r - eps M^-1 x, eps = x.M^-1 r / x.M^-1 x (so that the exact
+// block does not return t = -x).  From the reduced sums xsum[b] = (x.t1,
+// x.u): eps[b], and with dots the first pass's coefficients
+// V.t = V.t1 - eps V.u (coef holds V.t1, c2 V.u)
+__global__ void k32_olsen(const double* __restrict__ xsum, const double* __restrict__ c2, int m,
+                          int M, int dots, const int32_t* __restrict__ active,
+                          double* __restrict__ coef, float* __restrict__ eps) {
+  const int b = blockIdx.x;
+  if (!active[b]) return;
+  const double xu = xsum[(int64_t)b * 2 + 1];
+  double e = xsum[(int64_t)b * 2] / xu;
+  if (!(xu != 0.0) || !isfinite(e)) e = 0.0;
+  if (threadIdx.x == 0) eps[b] = (float)e;
+  if (dots)
+    for (int i = threadIdx.x; i < m; i += blockDim.x)
+      coef[(int64_t)b * M + i] -= e * c2[(int64_t)b * M + i];
+}
+
+// T <- T - eps U (Olsen's combination where the dots are taken afterwards)
+__global__ void k32_sub_eps(float* __restrict__ T, const float* __restrict__ U,
+                            const float* __restrict__ eps, int64_t N,
+                            const int32_t* __restrict__ active) {
+  const int b = blockIdx.y;
+  if (!active[b]) return;
+  const float e = eps[b];
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N;
+       k += (int64_t)gridDim.x * blockDim.x)
+    T[(int64_t)b * N + k] = fmaf(-e, U[(int64_t)b * N + k], T[(int64_t)b * N + k]);
 }
 
 // One classical Gram-Schmidt update T <- T - sum_{i<m} c_i V_i, with the dot
@@ -327,7 +386,9 @@ __global__ void __launch_bounds__(RT) k32_orth_pass(float* __restrict__ T,
                                                    const float* __restrict__ V, int m, int M,
                                                    int64_t N, const double* __restrict__ coef,
                                                    const int32_t* __restrict__ active, int norm,
-                                                   int nchunks, double* __restrict__ partial) {
+                                                   int nchunks, double* __restrict__ partial,
+                                                   const float* __restrict__ Uo,
+                                                   const float* __restrict__ eps) {
   const int b = blockIdx.y;
   if (!active[b]) return;
   __shared__ float sc[32];
@@ -341,8 +402,13 @@ __global__ void __launch_bounds__(RT) k32_orth_pass(float* __restrict__ T,
   const float* Vb = V + (int64_t)b * M * N;
   float* Tb = T + (int64_t)b * N;
   float nacc = 0.f;
+  // with Uo (first pass under Olsen's correction): T holds M^-1 r and the
+  // update starts from t = M^-1 r - eps M^-1 x
+  const float e = Uo ? eps[b] : 0.f;
+  const float* Ub = Uo ? Uo + (int64_t)b * N : nullptr;
   for (int64_t k = k0 + threadIdx.x; k < k1; k += RT) {
     float t = Tb[k];
+    if (Ub) t = fmaf(-e, Ub[k], t);
     for (int i = 0; i < m; i++) t = fmaf(-sc[i], Vb[(int64_t)i * N + k], t);
     Tb[k] = t;
     if (norm) {
@@ -696,6 +762,25 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
                                   (float)shift, hd.ptr);
     CU_LAUNCH_CHECK();
   }
+  // P-space preconditioner: the lowest-diagonal block of A solved exactly,
+  // with Olsen's correction (u = M^-1 x in U32, its dot partials in upart,
+  // x.M^-1 r and x.M^-1 x in xpart)
+  PspaceWork psp;
+  pspace_setup(ctx, bp, hd.ptr, shift, pspace_size(bp, ctx->opt.pspace), psp);
+  const bool olsen = psp.npp > 0;
+  DevBuf<float> U32(P, olsen ? (size_t)B * N : 0), epsb(P, olsen ? (size_t)B : 0);
+  DevBuf<double> upart(P, olsen ? (size_t)B * M * nchunks : 0),
+      xpart(P, olsen ? (size_t)B * 2 * nchunks : 0), xsum(P, olsen ? (size_t)B * 2 : 0),
+      coef2(P, olsen ? (size_t)B * M : 0);
+  {
+    // the residual kernel's dot accumulators: up to 2 x 32 x RT floats
+    static bool attr_done[64] = {false};
+    if (!attr_done[ctx->device & 63]) {
+      CU_CHECK(cudaFuncSetAttribute(k32_residual_pre, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    2 * 32 * RT * (int)sizeof(float)));
+      attr_done[ctx->device & 63] = true;
+    }
+  }
   k32_guess<<<B, 256, 0, st>>>(hd.ptr, bp.nstr, M, V.ptr);
   CU_LAUNCH_CHECK();
   if (plan) launch_parent_guess(ctx, *plan, bp.n, bp.nsig, bp.nstr, V.ptr, nullptr, (int64_t)M * N);
@@ -739,21 +824,46 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
   // orthogonalise T against V[0..m) twice (classical Gram-Schmidt), append
   // as V[m].  raw: T is an unpreconditioned residual; dots_ready: T is
   // preconditioned and `partial` holds the first pass's V_i . T partials
-  // (both from k32_residual_pre)
+  // (both from k32_residual_pre).  The P-space block of the correction is
+  // replaced first (the dot partials corrected with it).
   auto extend = [&](int m, bool raw, bool dots_ready) {
     if (raw) {
       k32_precondition<<<gpre, 256, 0, st>>>(T.ptr, hd.ptr, bp.nstr, theta.ptr, active.ptr);
       CU_LAUNCH_CHECK();
     }
-    if (dots_ready) {
+    // Olsen's combination goes with the P-space block (its exact block would
+    // return t = -x); the exact-point residual (raw) takes the plain block
+    const bool ols = olsen && !raw;
+    pspace_apply(ctx, bp, psp, T.ptr, hd.ptr, theta.ptr, V.ptr, m, M, nchunks, partial.ptr,
+                 dots_ready, active.ptr, ols, U32.ptr, X.ptr, upart.ptr, xpart.ptr);
+    if (ols) {
+      k32_final<<<B, 32, 0, st>>>(xpart.ptr, 2, nchunks, active.ptr, xsum.ptr, 2, 1);
+      CU_LAUNCH_CHECK();
+      if (dots_ready) {
+        k32_final<<<B, 32, 0, st>>>(partial.ptr, m, nchunks, active.ptr, coef.ptr, M, 1);
+        CU_LAUNCH_CHECK();
+        k32_final<<<B, 32, 0, st>>>(upart.ptr, m, nchunks, active.ptr, coef2.ptr, M, 1);
+        CU_LAUNCH_CHECK();
+      }
+      k32_olsen<<<B, 32, 0, st>>>(xsum.ptr, coef2.ptr, m, M, dots_ready ? 1 : 0, active.ptr,
+                                  coef.ptr, epsb.ptr);
+      CU_LAUNCH_CHECK();
+      if (!dots_ready) {
+        k32_sub_eps<<<ge, 256, 0, st>>>(T.ptr, U32.ptr, epsb.ptr, N, active.ptr);
+        CU_LAUNCH_CHECK();
+        dots(V.ptr, (int64_t)M * N, N, T.ptr, N, m, coef.ptr, M, 1, active.ptr);
+      }
+    } else if (dots_ready) {
       k32_final<<<B, 32, 0, st>>>(partial.ptr, m, nchunks, active.ptr, coef.ptr, M, 1);
       CU_LAUNCH_CHECK();
     } else {
       dots(V.ptr, (int64_t)M * N, N, T.ptr, N, m, coef.ptr, M, 1, active.ptr);
     }
     for (int pass = 0; pass < 2; pass++) {
+      const bool fold = ols && dots_ready && pass == 0;   // t = t1 - eps u inside the pass
       k32_orth_pass<<<gc, RT, 0, st>>>(T.ptr, V.ptr, m, M, N, coef.ptr, active.ptr, pass,
-                                      nchunks, partial.ptr);
+                                      nchunks, partial.ptr, fold ? U32.ptr : nullptr,
+                                      epsb.ptr);
       CU_LAUNCH_CHECK();
       k32_final<<<B, 32, 0, st>>>(partial.ptr, pass ? 1 : m, nchunks, active.ptr, coef.ptr, M,
                                   1);
@@ -786,9 +896,10 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
       CU_LAUNCH_CHECK();
       k32_jacobi<<<B, 32, 0, st>>>(G.ptr, m, M, active.ptr, theta.ptr, y.ptr);
       CU_LAUNCH_CHECK();
-      k32_residual_pre<<<gc, RT, 0, st>>>(V.ptr, AV.ptr, RX.ptr, exact0 ? 1 : 0, m, M, N,
-                                          y.ptr, theta.ptr, thx.ptr, hd.ptr, active.ptr, X.ptr,
-                                          T.ptr, nchunks, rpart.ptr, partial.ptr);
+      k32_residual_pre<<<gc, RT, (olsen ? 2 : 1) * m * RT * sizeof(float), st>>>(
+          V.ptr, AV.ptr, RX.ptr, exact0 ? 1 : 0, m, M, N, y.ptr, theta.ptr, thx.ptr, hd.ptr,
+          active.ptr, X.ptr, T.ptr, nchunks, rpart.ptr, partial.ptr, olsen ? 1 : 0, U32.ptr,
+          upart.ptr, xpart.ptr);
       CU_LAUNCH_CHECK();
       k32_converge<<<1, 256, 0, st>>>(rpart.ptr, nchunks, B, m_start > 1 ? it + 1 : it, tolr.ptr,
                                       rel, theta.ptr, rnorm.ptr, active.ptr, iters.ptr, nact.ptr);

@@ -230,6 +230,26 @@ struct BinProblem {
   DevBuf<uint8_t> gsplit;        // g' as bf16 hi/lo in the tensor-core operand layout
 };
 
+// P-space preconditioner of the mixed Davidson iteration (mbe_pspace.cu):
+// per tuple the npp lowest-diagonal symmetric basis functions, the
+// eigenvectors U and eigenvalues of A restricted to them
+struct PspaceWork {
+  int npp = 0;
+  DevBuf<int32_t> sel;   // B * 128 canonical determinant indices
+  DevBuf<float> lam;     // B * 128
+  DevBuf<float> U;       // B * 128 * 128
+};
+// the P-space size used for a bin (0: off) given the requested size
+int pspace_size(const BinProblem& bp, int requested);
+void pspace_setup(mbe_ctx* ctx, BinProblem& bp, const float* hd, double shift, int npp,
+                  PspaceWork& w);
+// the P-space block of t (and with olsen of u = M^-1 x in Uo, X the Ritz
+// vector), correcting the partial dot products that the residual kernel left
+void pspace_apply(mbe_ctx* ctx, const BinProblem& bp, const PspaceWork& w, float* T,
+                  const float* hd, const double* theta, const float* V, int m, int M,
+                  int nchunks, double* partial, bool fix_dots, const int32_t* active,
+                  bool olsen, float* Uo, const float* X, double* upart, double* xpart);
+
 // ------------------------------------------------------------ launchers
 void build_string_tables(mbe_ctx* ctx, StringTables* t);
 // raw-pointer forms of the table, integral and FP64 sigma launchers (they

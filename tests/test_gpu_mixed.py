@@ -209,3 +209,31 @@ def test_sigma_exact_fused_elementwise(lib, case):
     s2 = sig.reshape(sp.nstr, sp.nstr)
     assert np.array_equal(s2, s2.T)
     m.close()
+
+
+def test_pspace_preconditioner_same_energies_fewer_iterations(lib):
+    """The P-space block (the 128 lowest-diagonal symmetric functions solved
+    exactly in the Davidson correction) changes the path of the iteration,
+    not its limit: seeded order-4 tuples of the 8e/23o workload (8e/10o
+    CASCIs) give the energies of the diagonal preconditioner and the
+    oracle's, in fewer iterations."""
+    w = ms.workload("h2o_dz_8e23o")
+    h, eri, _ = ms.workload_integrals("h2o_dz_8e23o")
+    rest = [o for o in w["exp"] if o != 0]
+    tuples = np.array([(0,) + t for t in ms.sample_tuples(rest, 3, 12, 31)], dtype=np.int32)
+    out = {}
+    for psp in (0, 128):
+        m = mixed(lib, pspace=psp)
+        m.load(h, eri, w["nel"])
+        lib.mbe_set_reference(m.ctx, w["ref"], w["exp"])
+        lib.mbe_reset_stats(m.ctx)
+        eps, st = lib.mbe_solve_tuples(m.ctx, tuples, 4)
+        assert np.all(st == 0)
+        out[psp] = (eps, lib.mbe_get_stats(m.ctx)["iters_total"])
+        m.close()
+    (e0, it0), (e1, it1) = out[0], out[128]
+    assert np.max(np.abs(e0 - e1)) < 1e-9
+    assert it1 < it0, (it1, it0)
+    for t, e in list(zip(tuples, e1))[:3]:
+        e_or = oc.casci(h, eri, w["nocc"], om.active_space(w["ref"], tuple(t)))
+        assert abs(e - e_or) < TOL_MIXED_EPS, (t, e, e_or)
