@@ -259,6 +259,32 @@ __device__ __forceinline__ void sd_sums_to_partial(const float (*sD)[RT], int m,
   }
 }
 
+// the same for pairs of accumulators: .x to partial, .y to partial2
+__device__ __forceinline__ void sde_sums_to_partial(const float2 (*sDE)[RT], int m,
+                                                    double* __restrict__ partial,
+                                                    double* __restrict__ partial2, int b,
+                                                    int chunk, int nchunks) {
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = warp; i < m; i += RT / 32) {
+    double v = 0.0, w = 0.0;
+#pragma unroll
+    for (int j = 0; j < RT / 32; j++) {
+      const float2 a = sDE[i][lane + 32 * j];
+      v += (double)a.x;
+      w += (double)a.y;
+    }
+    for (int off = 16; off; off >>= 1) {
+      v += __shfl_down_sync(0xffffffffu, v, off);
+      w += __shfl_down_sync(0xffffffffu, w, off);
+    }
+    if (lane == 0) {
+      partial[((int64_t)b * m + i) * nchunks + chunk] = v;
+      partial2[((int64_t)b * m + i) * nchunks + chunk] = w;
+    }
+  }
+}
+
 // The residual step with the preconditioner and the first orthogonalisation
 // pass's dot products folded in:
 //   x = V y,  r = AV y - theta x (stage A), or with exact0
@@ -279,16 +305,17 @@ __global__ void __launch_bounds__(RT) k32_residual_pre(
     double* __restrict__ upart, double* __restrict__ xpart) {
   const int b = blockIdx.y;
   if (!active[b]) return;
-  // per-thread dot accumulators: sD[i] for V_i . t, with olsen sE[i] for V_i . u
+  // per-thread dot accumulators: sD[i] for V_i . t, or with olsen sDE[i] for
+  // (V_i . t, V_i . u) (one 8-byte shared access per vector and element)
   extern __shared__ float sdyn[];
   float (*sD)[RT] = reinterpret_cast<float (*)[RT]>(sdyn);
-  float (*sE)[RT] = reinterpret_cast<float (*)[RT]>(sdyn + m * RT);
+  float2 (*sDE)[RT] = reinterpret_cast<float2 (*)[RT]>(sdyn);
   __shared__ float sy[32];
   __shared__ double red[32];
   if (threadIdx.x < m) sy[threadIdx.x] = (float)y[(int64_t)b * M + threadIdx.x];
   for (int i = 0; i < m; i++) {
-    sD[i][threadIdx.x] = 0.f;
-    if (olsen) sE[i][threadIdx.x] = 0.f;
+    if (olsen) sDE[i][threadIdx.x] = make_float2(0.f, 0.f);
+    else sD[i][threadIdx.x] = 0.f;
   }
   __syncthreads();
   const float th = (float)theta[b];
@@ -324,8 +351,10 @@ __global__ void __launch_bounds__(RT) k32_residual_pre(
       xu = fmaf(x, u, xu);
       for (int i = 0; i < m; i++) {
         const float v = Vb[(int64_t)i * N + k];
-        sD[i][threadIdx.x] = fmaf(v, t, sD[i][threadIdx.x]);
-        sE[i][threadIdx.x] = fmaf(v, u, sE[i][threadIdx.x]);
+        float2 a = sDE[i][threadIdx.x];
+        a.x = fmaf(v, t, a.x);
+        a.y = fmaf(v, u, a.y);
+        sDE[i][threadIdx.x] = a;
       }
     } else {
       for (int i = 0; i < m; i++)
@@ -341,9 +370,10 @@ __global__ void __launch_bounds__(RT) k32_residual_pre(
     __syncthreads();
     const double s_xu = block_sum((double)xu, red);
     if (threadIdx.x == 0) xpart[((int64_t)b * 2 + 1) * nchunks + blockIdx.x] = s_xu;
-    sd_sums_to_partial(sE, m, upart, b, blockIdx.x, nchunks);
+    sde_sums_to_partial(sDE, m, dpart, upart, b, blockIdx.x, nchunks);
+  } else {
+    sd_sums_to_partial(sD, m, dpart, b, blockIdx.x, nchunks);
   }
-  sd_sums_to_partial(sD, m, dpart, b, blockIdx.x, nchunks);
 }
 
 // Olsen's correction with the P-space preconditioner M = theta - A_0:
