@@ -4,6 +4,8 @@ tuples), on sampled outputs.
 
 * 8e/114o (CAS(8e,8o) reference over orbitals 0-7, 106 expansion orbitals):
   seeded order-1 and order-2 tuples against the oracle, one CASCI at a time.
+* 8e/23o stretched (near-degenerate virtuals): seeded tuples of orders 1-3
+  against the oracle, FP64 and mixed.
 * 10e/60o hydrogen-chain-shaped (CAS(10e,10o) reference): the CASCIs
   (10e/11o = 213,444 and 10e/12o = 627,264 determinants) are beyond the
   oracle's test time, so the mixed path is checked against the FP64 path,
@@ -73,3 +75,22 @@ def test_h10_10e60o_sampled_tuples_mixed_vs_fp64(lib):
     # variational ordering: reference >= order 1 (t1[0]) >= order 2 (t1[0] + o)
     assert np.all(e1_d <= e_ref_d + 1e-12)
     assert np.all(e2_d <= e1_d[0] + 1e-12)
+
+
+def test_stretched_8e23o_sampled_tuples_vs_oracle(lib):
+    """The near-degenerate variant of the 8e/23o workload (virtual orbital
+    energies compressed into [0.02, 0.6] Eh): seeded tuples of orders 1-3,
+    FP64 and mixed paths against the oracle's CASCI energies."""
+    name = "h2o_dz_8e23o_stretched"
+    w = ms.workload(name)
+    h, eri, _ = ms.workload_integrals(name)
+    for order, count, seed in ((1, 2, 51), (2, 2, 52), (3, 1, 53)):
+        tuples = ms.sample_tuples(w["exp"], order, count, seed)
+        e_ref_m, eps_m = solve(lib, name, tuples, order, lib.MBE_MIXED_BF16X3)
+        e_ref_d, eps_d = solve(lib, name, tuples, order, lib.MBE_FP64)
+        assert abs(e_ref_d - oc.casci(h, eri, w["nocc"], w["ref"])) < 1e-10
+        assert abs(e_ref_m - e_ref_d) < 1e-8
+        for t, em, ed in zip(tuples, eps_m, eps_d):
+            eo = oc.casci(h, eri, w["nocc"], om.active_space(w["ref"], t))
+            assert abs(ed - eo) < 1e-10, (t, ed, eo)
+            assert abs(em - eo) < 1e-8, (t, em, eo)
