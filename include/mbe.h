@@ -58,12 +58,16 @@ enum {
 /* Precision of the sigma-vector contraction. */
 enum {
   MBE_FP64 = 0,          /* every step in FP64 (CUDA-core FP64 contraction)  */
-  MBE_MIXED_BF16X3 = 1,  /* Davidson sigma vectors as split-BF16x3 on tcgen05
-                            tensor cores with FP32 accumulation (fused
-                            gather/contraction/scatter); refinement rounds and
-                            the final Rayleigh quotient with FP64-grade sigma
-                            vectors (MBE_EMULATED_FP64 contraction); Ritz
-                            step, orthogonalisation and sums in FP64          */
+  MBE_MIXED_BF16X3 = 1,  /* Davidson vectors in FP32; their sigma vectors as
+                            split-BF16x3 on tcgen05 tensor cores with FP32
+                            accumulation; refinement rounds ("exact points")
+                            with FP64-grade sigma vectors, the Rayleigh
+                            quotient and residual formed with error-free
+                            FP32 products and sums; the Ritz step is an FP32
+                            Jacobi eigensolver refined by FP64 Newton steps,
+                            Gram-Schmidt runs in FP32 with FP64 sums across
+                            threads, the energy, <S^2> and the increment
+                            sums are FP64                                    */
   MBE_EMULATED_FP64 = 2  /* every sigma vector with the (kl|ij) contraction
                             emulated to ~1e-10 relative on tcgen05 tensor
                             cores (exact 8-bit slices, grouped FP32
@@ -273,8 +277,12 @@ int mbe_sigma(mbe_ctx* ctx, const int* act, int nact, const double* c,
  * A problem that does not fit (roughly more than 9 active orbitals) returns
  * MBE_EINVAL and launches nothing.  Calls overlapping on one device race on
  * that array: issue them on one stream or wait for one before the next.
- * The first call on a device looks the array up (cudaGetSymbolAddress) and
- * sets a kernel attribute; make it before any stream capture. */
+ * The first call on a device looks the array up (cudaGetSymbolAddress),
+ * sets a kernel attribute and copies a small constant table with a
+ * synchronous cudaMemcpyToSymbol (once per device, shared with the other
+ * entry points); make it before any stream capture.  The active orbitals
+ * reach the device as a kernel argument; with e_core non-NULL the call
+ * copies the core energy to the host and waits for the stream. */
 int mbe_sigma_noalloc(mbe_ctx* ctx, const int* act, int nact, const double* c_dev,
                       double* sigma_dev, int64_t ndet, double* e_core);
 

@@ -51,11 +51,13 @@ def lib():
         i, l = ctypes.c_int, ctypes.c_long
         L.oracle_hdiag.argtypes = [i, dp, dp, l, up, l, up, dp]
         L.oracle_sigma.argtypes = [i, dp, dp, l, up, l, up, dp, dp]
+        L.oracle_sigma_rows.argtypes = [i, dp, dp, l, up, l, up, dp, l,
+                                        ctypes.POINTER(ctypes.c_long), dp]
         L.oracle_hdense.argtypes = [i, dp, dp, l, up, l, up, dp]
         L.oracle_rdm12.argtypes = [i, l, up, l, up, dp, dp, dp]
         L.oracle_s2.argtypes = [i, l, up, l, up, dp, dp, dp]
-        for f in (L.oracle_hdiag, L.oracle_sigma, L.oracle_hdense, L.oracle_rdm12,
-                  L.oracle_s2):
+        for f in (L.oracle_hdiag, L.oracle_sigma, L.oracle_sigma_rows, L.oracle_hdense,
+                  L.oracle_rdm12, L.oracle_s2):
             f.restype = None
         _lib = L
     return _lib
@@ -115,6 +117,18 @@ class Space:
         out = np.empty(self.ndet)
         lib().oracle_sigma(self.norb, _dp(self.h), _dp(self.eri), self.nstr, _up(self.strs),
                            self.nstr, _up(self.strs), _dp(c), _dp(out))
+        return out
+
+    def sigma_rows(self, c, rows):
+        """(H c)_I for the determinant indices I in ``rows`` only."""
+        c = np.ascontiguousarray(c, dtype=np.float64).ravel()
+        rows = np.ascontiguousarray(rows, dtype=np.int64).ravel()
+        if rows.size and (rows.min() < 0 or rows.max() >= self.ndet):
+            raise ValueError("row index out of range")
+        out = np.empty(rows.size)
+        lib().oracle_sigma_rows(self.norb, _dp(self.h), _dp(self.eri), self.nstr,
+                                _up(self.strs), self.nstr, _up(self.strs), _dp(c), rows.size,
+                                rows.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), _dp(out))
         return out
 
     def hdense(self):

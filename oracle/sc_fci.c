@@ -240,6 +240,23 @@ void oracle_sigma(int norb, const double *h, const double *eri,
         }
 }
 
+/* sigma_I for the listed determinants only: out[x] = sum_J <I|H|J> c_J with
+ * I = rows[x] (the loop of oracle_sigma restricted to those rows). */
+void oracle_sigma_rows(int norb, const double *h, const double *eri,
+                       long na, const uint64_t *astr, long nb, const uint64_t *bstr,
+                       const double *c, long nrows, const long *rows, double *out) {
+    ints_t I = {norb, (long)norb * (norb + 1) / 2, h, eri};
+    space_t S; setup_space(&S, &I, na, astr, nb, bstr);
+    #pragma omp parallel for schedule(dynamic, 4)
+    for (long x = 0; x < nrows; x++) {
+        long i = rows[x];
+        sdet d = make_det(astr + 2 * (i / nb), bstr + 2 * (i % nb));
+        sig_ctx sc = {c, 0.0};
+        for_each_connected(&S, &d, sig_visit, &sc);
+        out[x] = sc.acc + diag_elem(&I, &d) * c[i];
+    }
+}
+
 typedef struct { double *row; } row_ctx;
 static void row_visit(void *ctx, long j, double hji) { ((row_ctx *)ctx)->row[j] += hji; }
 

@@ -314,7 +314,8 @@ int mbe_create(mbe_ctx** out, int device, const mbe_options* opt) {
       !(o.mixed_rel_tol > 0.0) || o.pspace < 0 || o.pspace > 128)
     return MBE_EINVAL;
   int ndev = 0;
-  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+  if (device < 0 || device >= MBE_MAX_DEVICES) return MBE_EINVAL;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device >= ndev) {
     cudaGetLastError();
     return MBE_ECUDA;
   }

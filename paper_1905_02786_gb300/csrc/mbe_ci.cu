@@ -22,22 +22,24 @@ namespace {
 
 __constant__ int c_binom[33][33];
 
-bool g_binom_ready[64] = {false};
+bool g_binom_ready[MBE_MAX_DEVICES] = {false};
 
+// the binomial table is copied with a synchronous cudaMemcpyToSymbol on the
+// first use on a device (it waits for the device once)
 void ensure_binom(int device) {
-  if (g_binom_ready[device]) return;
-  int tab[33][33];
-  for (int n = 0; n <= 32; n++)
-    for (int k = 0; k <= 32; k++) {
-      if (k == 0) tab[n][k] = 1;
-      else if (n == 0) tab[n][k] = 0;
-      else {
-        long long v = (long long)tab[n - 1][k - 1] + tab[n - 1][k];
-        tab[n][k] = v > 0x7fffffff ? 0x7fffffff : (int)v;
+  once_per_device(g_binom_ready, device, [] {
+    int tab[33][33];
+    for (int n = 0; n <= 32; n++)
+      for (int k = 0; k <= 32; k++) {
+        if (k == 0) tab[n][k] = 1;
+        else if (n == 0) tab[n][k] = 0;
+        else {
+          long long v = (long long)tab[n - 1][k - 1] + tab[n - 1][k];
+          tab[n][k] = v > 0x7fffffff ? 0x7fffffff : (int)v;
+        }
       }
-    }
-  CU_CHECK(cudaMemcpyToSymbol(c_binom, tab, sizeof(tab)));
-  g_binom_ready[device] = true;
+    CU_CHECK(cudaMemcpyToSymbol(c_binom, tab, sizeof(tab)));
+  });
 }
 
 // colexicographic rank of a k-subset bit mask = its position when all
@@ -632,12 +634,11 @@ void sigma_fp64_raw(mbe_ctx* ctx, int n, int nsig, int nstr, const int32_t* link
   int64_t blocks = (ndet + 255) / 256;
   if (blocks > 2048) blocks = 2048;
   const size_t smem_c = sizeof(double) * (npair * npair + npair * GT_N);
-  static bool attr_set[64] = {false};
-  if (!attr_set[ctx->device]) {
+  static bool attr_set[MBE_MAX_DEVICES] = {false};
+  once_per_device(attr_set, ctx->device, [] {
     CU_CHECK(cudaFuncSetAttribute(k_contract_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   200 * 1024));
-    attr_set[ctx->device] = true;
-  }
+  });
   int64_t cblocks = (ndet + GT_N - 1) / GT_N;
   if (cblocks > 1024) cblocks = 1024;
   const dim3 g1((unsigned)blocks, nb);

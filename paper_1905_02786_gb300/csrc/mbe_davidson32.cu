@@ -804,12 +804,11 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
       coef2(P, olsen ? (size_t)B * M : 0);
   {
     // the residual kernel's dot accumulators: up to 2 x 32 x RT floats
-    static bool attr_done[64] = {false};
-    if (!attr_done[ctx->device & 63]) {
+    static bool attr_done[MBE_MAX_DEVICES] = {false};
+    once_per_device(attr_done, ctx->device, [] {
       CU_CHECK(cudaFuncSetAttribute(k32_residual_pre, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     2 * 32 * RT * (int)sizeof(float)));
-      attr_done[ctx->device & 63] = true;
-    }
+    });
   }
   k32_guess<<<B, 256, 0, st>>>(hd.ptr, bp.nstr, M, V.ptr);
   CU_LAUNCH_CHECK();

@@ -418,14 +418,13 @@ void sigma_exact(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const float* c, int
                                                              w.gexp.ptr);
     CU_LAUNCH_CHECK();
   }
-  static bool attr_done[64] = {false};
-  if (!attr_done[ctx->device]) {
+  static bool attr_done[MBE_MAX_DEVICES] = {false};
+  once_per_device(attr_done, ctx->device, [] {
     CU_CHECK(cudaFuncSetAttribute(k_sigma_exact<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   227 * 1024 - 1024));
     CU_CHECK(cudaFuncSetAttribute(k_sigma_exact<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   227 * 1024 - 1024));
-    attr_done[ctx->device] = true;
-  }
+  });
   const dim3 grid((unsigned)((nstr + R - 1) / R), bp.B);
   cudaEvent_t ev;
   ctx->fp64_timer.begin(ctx->stream, ctx->opt.timing != 0, &ev);

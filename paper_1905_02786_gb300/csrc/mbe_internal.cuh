@@ -7,11 +7,13 @@
 #include <map>
 #include <memory>
 #include <unordered_map>
+#include <mutex>
 #include "../../include/mbe.h"
 
 #define MBE_MAX_ACT 30      // active orbitals per CASCI (string masks are uint32)
 #define MBE_MAX_NORB 128    // tuple keys are 128-bit orbital sets
 #define MBE_MAX_ORDER 16    // increments enumerate 2^order - 2 subtuples
+#define MBE_MAX_DEVICES 64  // per-device one-time set-up flags (mbe_create checks)
 
 // ---------------------------------------------------------------- errors
 struct MbeError {
@@ -26,6 +28,20 @@ struct MbeError {
       throw MbeError{MBE_ECUDA, std::string(#call) + ": " +                 \
                                     cudaGetErrorString(e_)};                \
   } while (0)
+
+// Runs f() once per device for the flag array `done` (a kernel attribute, a
+// constant table): the check and the set-up are serialised by one mutex per
+// call site, so that contexts on several host threads may race to it.
+template <class F>
+void once_per_device(bool (&done)[MBE_MAX_DEVICES], int device, F f) {
+  static std::mutex mu;
+  if (device < 0 || device >= MBE_MAX_DEVICES)
+    throw MbeError{MBE_EINVAL, "device index out of range"};
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[device]) return;
+  f();
+  done[device] = true;
+}
 
 // every launch site checks the launch and counts it
 extern int64_t g_mbe_launches;

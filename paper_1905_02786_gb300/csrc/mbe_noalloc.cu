@@ -22,7 +22,10 @@
 //
 // The first call on a device resolves the scratch address with
 // cudaGetSymbolAddress and sets the contraction kernel's shared-memory
-// attribute; it should come before any stream capture.
+// attribute; it should come before any stream capture.  The active orbitals
+// reach the scratch through a kernel argument (no host-memory copy); with a
+// non-NULL e_core the call copies the core energy back and waits for the
+// stream.
 #include "mbe_internal.cuh"
 #include <algorithm>
 #include <mutex>
@@ -32,10 +35,10 @@ namespace {
 static __device__ __align__(256) unsigned char g_sigma_scratch[MBE_NOALLOC_SCRATCH_BYTES];
 
 std::mutex g_scratch_mu;
-void* g_scratch_ptr[64] = {nullptr};
+void* g_scratch_ptr[MBE_MAX_DEVICES] = {nullptr};
 
 unsigned char* scratch_base(int device) {
-  if (device < 0 || device >= 64) throw MbeError{MBE_EINVAL, "device index out of range"};
+  if (device < 0 || device >= MBE_MAX_DEVICES) throw MbeError{MBE_EINVAL, "device index out of range"};
   std::lock_guard<std::mutex> lk(g_scratch_mu);
   if (!g_scratch_ptr[device]) {
     void* p = nullptr;
@@ -76,6 +79,16 @@ NoallocLayout noalloc_layout(int n, int64_t nstr) {
   return L;
 }
 
+// the sorted active orbitals (at most 15) passed by value
+struct ActList {
+  int32_t v[16];
+};
+__global__ void k_put_act(ActList a, int n, int32_t* __restrict__ dst, int32_t* __restrict__ bmap) {
+  const int t = threadIdx.x;
+  if (t < n) dst[t] = a.v[t];
+  if (t == 0) bmap[0] = 0;
+}
+
 }  // namespace
 
 int noalloc_sigma_run(mbe_ctx* ctx, const int* act, int nact, const double* c_dev,
@@ -103,8 +116,10 @@ int noalloc_sigma_run(mbe_ctx* ctx, const int* act, int nact, const double* c_de
   int32_t* bmap = (int32_t*)(base + L.bmap);
   double* ecore = (double*)(base + L.ecore);
   cudaStream_t st = ctx->stream;
-  CU_CHECK(cudaMemcpyAsync(actd, a.data(), sizeof(int32_t) * nact, cudaMemcpyHostToDevice, st));
-  CU_CHECK(cudaMemsetAsync(bmap, 0, sizeof(int32_t), st));
+  ActList al = {};
+  for (int i = 0; i < nact; i++) al.v[i] = a[i];
+  k_put_act<<<1, 32, 0, st>>>(al, nact, actd, bmap);
+  CU_LAUNCH_CHECK();
   launch_string_tables(ctx, nact, nsig, (int)nstr, masks, link);
   launch_effints_raw(ctx, actd, 1, nact, nsig, ecore, (double*)(base + L.heff),
                      (double*)(base + L.hp), (double*)(base + L.gp), (double*)(base + L.jk));

@@ -288,12 +288,11 @@ void contract_ozaki(mbe_ctx* ctx, const double* gp, int npair, const double* D, 
                     int32_t* err) {
   const int kpad = ((npair + 15) / 16) * 16;
   const OzLayout L = oz_layout(kpad);
-  static int attr_done[64] = {0};
-  if (!attr_done[ctx->device]) {
+  static bool attr_done[MBE_MAX_DEVICES] = {false};
+  once_per_device(attr_done, ctx->device, [] {
     CU_CHECK(cudaFuncSetAttribute(k_contract_ozaki, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   227 * 1024 - 1024));
-    attr_done[ctx->device] = 1;
-  }
+  });
   int64_t ntiles = (ndet + OZ_N - 1) / OZ_N;
   // enough CTAs to fill the GPU; each CTA reuses its g' slices for its tiles
   int64_t per_tuple = std::max<int64_t>(1, std::min<int64_t>(ntiles, (2 * 152 + nb - 1) / nb));

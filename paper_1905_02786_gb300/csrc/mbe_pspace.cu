@@ -527,14 +527,13 @@ void pspace_setup(mbe_ctx* ctx, BinProblem& bp, const float* hd, double shift, i
   k_psp_select<<<B, SEL_THREADS, 0, st>>>(hd, bp.nstr, npp, w.sel.ptr);
   CU_LAUNCH_CHECK();
   const uint32_t smem = eig_layout(bp.n).total;
-  static bool attr_set[64] = {false};
-  if (!attr_set[ctx->device & 63]) {
+  static bool attr_set[MBE_MAX_DEVICES] = {false};
+  once_per_device(attr_set, ctx->device, [] {
     CU_CHECK(cudaFuncSetAttribute(k_psp_eigh, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   227 * 1024 - 4096));
     CU_CHECK(cudaFuncSetAttribute(k_psp_apply, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   PSP_MAX * PSP_PITCH * 4));
-    attr_set[ctx->device & 63] = true;
-  }
+  });
   k_psp_eigh<<<B, EIG_THREADS, smem, st>>>(bp.tab->masks.ptr, bp.nstr, bp.n, bp.nsig,
                                            bp.heff.ptr, bp.hp.ptr, bp.gp.ptr, hd, (float)shift,
                                            npp, w.sel.ptr, w.lam.ptr, w.U.ptr);

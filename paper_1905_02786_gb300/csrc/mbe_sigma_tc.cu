@@ -444,12 +444,11 @@ template <int R, int KP>
 void launch_tc_kp(int device, dim3 grid, uint32_t smem, cudaStream_t st, const int32_t* link,
                   int nstr, int npair, const uint8_t* gsplit, const float* c, int64_t c_stride,
                   const int32_t* active, float* X, int64_t x_stride, int32_t* err) {
-  static bool attr_done[64] = {false};
-  if (!attr_done[device]) {
+  static bool attr_done[MBE_MAX_DEVICES] = {false};
+  once_per_device(attr_done, device, [] {
     CU_CHECK(cudaFuncSetAttribute(k_sigma_tc<R, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   227 * 1024 - 1024));
-    attr_done[device] = true;
-  }
+  });
   k_sigma_tc<R, KP><<<grid, TC_THREADS, smem, st>>>(link, nstr, npair, gsplit, c, c_stride,
                                                     active, X, x_stride, err);
 }

@@ -1,0 +1,120 @@
+"""Error paths of the C ABI on the GPU: every documented failure returns its
+code (no abort, no device fault) and leaves the process able to continue.
+
+* MBE_ENOCONV: a Davidson iteration cap too small to converge; the energies
+  are still written and status_out marks every unconverged tuple.
+* MBE_ELOOKUP: the increments of an order whose subtuples were never
+  processed (Eq. 3 needs the increment of every proper subtuple).
+* MBE_ENOMEM: a device-memory cap below what one CASCI needs.
+After each failure a fresh context solves the same tuples correctly.
+"""
+import numpy as np
+import pytest
+
+import mbe_synth as ms
+from oracle import casci as oc
+from oracle import mbe as om
+
+pytestmark = pytest.mark.gpu
+
+# 8 electrons in 23 orbitals (orbitals 0-3 occupied); the reference space is
+# the doubly occupied orbital 3 alone (one determinant, exact at the first
+# Davidson iteration), so that only the tuples meet the iteration cap
+REF = [3]
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1905_02786_gb300 import build, _binding
+    build.build()
+    _binding.load_library()
+    return _binding
+
+
+@pytest.fixture(scope="module")
+def system():
+    name = "h2o_dz_8e23o"
+    w = ms.workload(name)
+    h, eri, _ = ms.workload_integrals(name)
+    exp = [o for o in range(w["norb"]) if o not in REF]
+    return w, h, eri, exp
+
+
+def _oracle(w, h, eri, t):
+    return oc.casci(h, eri, w["nocc"], om.active_space(REF, t))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_noconv_returns_status(lib, system, precision):
+    w, h, eri, exp = system
+    prec = lib.MBE_FP64 if precision == "fp64" else lib.MBE_MIXED_BF16X3
+    tuples = np.array([(0, 1, 7, 8), (1, 2, 9, 10), (0, 2, 7, 11)], dtype=np.int32)
+    m = lib.MBE(0, precision=prec, max_iter=2)
+    m.load(h, eri, w["nel"])
+    e_ref = lib.mbe_set_reference(m.ctx, REF, exp)
+    assert abs(e_ref - oc.casci(h, eri, w["nocc"], REF)) < 1e-10
+    eps, st = lib.mbe_solve_tuples(m.ctx, tuples, 4, allow_noconv=True)
+    with pytest.raises(lib.MBEError) as ei:
+        lib.mbe_solve_tuples(m.ctx, tuples, 4)
+    assert ei.value.code == lib.MBE_ENOCONV
+    m.close()
+    assert np.all(st == lib.MBE_ENOCONV), st
+    assert np.all(np.isfinite(eps))
+    # a variational upper bound of the converged energies
+    e_or = np.array([_oracle(w, h, eri, tuple(t)) for t in tuples])
+    assert np.all(eps >= e_or - 1e-8)
+    # the same tuples with the default cap converge to the oracle
+    m = lib.MBE(0, precision=prec)
+    m.load(h, eri, w["nel"])
+    lib.mbe_set_reference(m.ctx, REF, exp)
+    eps2, st2 = lib.mbe_solve_tuples(m.ctx, tuples, 4)
+    m.close()
+    assert np.all(st2 == 0)
+    tol = 1e-10 if precision == "fp64" else 1e-8
+    assert np.max(np.abs(eps2 - e_or)) < tol
+
+
+def test_missing_subtuple_is_elookup(lib, system):
+    w, h, eri, exp = system
+    m = lib.MBE(0)
+    m.load(h, eri, w["nel"])
+    lib.mbe_set_reference(m.ctx, REF, exp)
+    t1 = np.array([(0,), (7,)], dtype=np.int32)
+    lib.mbe_set_order_energies(m.ctx, t1, np.array([-1.0, -2.0]), 1)
+    lib.mbe_increments(m.ctx, 1, 0.0, 2)
+    # (0, 8) needs the order-1 increment of (8,), never processed
+    lib.mbe_set_order_energies(m.ctx, np.array([(0, 8)], dtype=np.int32), np.array([-3.0]), 2)
+    with pytest.raises(lib.MBEError) as ei:
+        lib.mbe_increments(m.ctx, 2, 0.0, 1)
+    assert ei.value.code == lib.MBE_ELOOKUP
+    assert "missing" in lib.mbe_last_error(m.ctx)
+    # the context stays usable: a complete order 2 assembles
+    lib.mbe_set_order_energies(m.ctx, np.array([(0, 7)], dtype=np.int32), np.array([-3.5]), 2)
+    inc, keep, e2, etot = lib.mbe_increments(m.ctx, 2, 0.0, 1)
+    m.close()
+    e_ref = oc.casci(h, eri, w["nocc"], REF)
+    d0, d7 = -1.0 - e_ref, -2.0 - e_ref
+    assert abs(inc[0] - (-3.5 - e_ref - d0 - d7)) < 1e-12
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_memory_cap_is_enomem(lib, system, precision):
+    w, h, eri, exp = system
+    prec = lib.MBE_FP64 if precision == "fp64" else lib.MBE_MIXED_BF16X3
+    # 8e/12o CASCIs (245,025 determinants): the Davidson subspace alone is
+    # tens of MB, far above a 4 MB cap
+    tuples = np.array([(0, 7, 8, 9, 10, 11)], dtype=np.int32)
+    m = lib.MBE(0, precision=prec, mem_cap_bytes=4 << 20)
+    m.load(h, eri, w["nel"])
+    lib.mbe_set_reference(m.ctx, REF, exp)
+    with pytest.raises(lib.MBEError) as ei:
+        lib.mbe_solve_tuples(m.ctx, tuples, 6)
+    assert ei.value.code == lib.MBE_ENOMEM
+    m.close()
+    _ok = lib.MBE(0, precision=prec)
+    _ok.load(h, eri, w["nel"])
+    lib.mbe_set_reference(_ok.ctx, REF, exp)
+    eps, st = lib.mbe_solve_tuples(_ok.ctx, np.array([(0, 7)], dtype=np.int32), 2)
+    _ok.close()
+    assert np.all(st == 0)
+    assert abs(eps[0] - _oracle(w, h, eri, (0, 7))) < 1e-8

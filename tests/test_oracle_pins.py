@@ -289,3 +289,26 @@ def test_gradient_central_fd():
         fd = (energy(h, ep) - energy(h, em)) / (2 * step)
         an = dg[a, b] * (1 if a == b else 2)
         assert abs(fd - an) <= 1e-6 * abs(an) + 1e-8
+
+
+def test_sigma_rows_equals_dense_rows():
+    """The oracle's sigma on a listed set of determinants equals the same
+    rows of the dense Slater-Condon matrix times c (Sec. 2: the CASCI
+    Hamiltonian of one tuple, inactive core and deleted virtuals included),
+    and the full-vector sigma at those rows; a row index outside the space
+    is rejected."""
+    n, nocc = 7, 3
+    h, eri, _ = ms.gen_integrals(n, nocc, 11)
+    act = [1, 2, 3, 4, 6]                      # orbital 0 inactive, 5 deleted
+    sp = oc.Space(h, eri, nocc, act)
+    rng = np.random.default_rng(4)
+    c = rng.standard_normal(sp.ndet)
+    rows = rng.choice(sp.ndet, size=min(40, sp.ndet), replace=False)
+    rows = np.concatenate([rows, [0, sp.ndet - 1]])
+    H = sp.hdense()
+    got = sp.sigma_rows(c, rows)
+    assert np.abs(got - H[rows] @ c).max() < 1e-12 * max(1.0, np.abs(H).max())
+    assert np.array_equal(got, sp.sigma(c)[rows])
+    assert sp.sigma_rows(c, np.array([], dtype=np.int64)).size == 0
+    with pytest.raises(ValueError):
+        sp.sigma_rows(c, [sp.ndet])
