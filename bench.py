@@ -125,13 +125,32 @@ def oracle_sample_rate(w, h, eri, ntup_per_order=2, orders=(1, 2, 3), seed=7):
     for k in orders:
         sample += ms.sample_tuples(w["exp"], k, ntup_per_order, seed + k)
     t0 = time.perf_counter()
+    per_order = {}
     for t in sample:
+        t1 = time.perf_counter()
         oc.casci(h, eri, w["nocc"], om.active_space(w["ref"], t))
+        per_order.setdefault(len(t), []).append(time.perf_counter() - t1)
     dt = time.perf_counter() - t0
     desc = (f"{len(sample)} seeded random tuples ({ntup_per_order} each of orders "
             f"{list(orders)}) of {w['name']}, each CASCI solved by the oracle; higher orders "
             f"are larger, so the oracle's rate on the full expansion is lower")
-    return len(sample) / dt, dt, desc, cores
+    sec = {k: sum(v) / len(v) for k, v in per_order.items()}
+    return len(sample) / dt, dt, desc, cores, sec
+
+
+def oracle_sigma_seconds(w, h, eri, order, seed=5):
+    """Seconds of one oracle sigma vector (Slater-Condon, determinant-driven,
+    all host cores) on the CASCI of one seeded tuple of `order` containing
+    orbital 0 (the largest bin of that order), and its determinant count."""
+    from oracle import casci as oc
+    from oracle import mbe as om
+    rest = [o for o in w["exp"] if o != 0]
+    t = (0,) + ms.sample_tuples(rest, order - 1, 1, seed)[0]
+    sp = oc.Space(h, eri, w["nocc"], om.active_space(w["ref"], t))
+    c = np.random.default_rng(seed).standard_normal(sp.ndet)
+    t0 = time.perf_counter()
+    sp.sigma(c)
+    return time.perf_counter() - t0, sp.ndet
 
 
 def run_reference(args):
@@ -144,8 +163,8 @@ def run_reference(args):
         oracle_sample_rate(w, h, eri, ntup_per_order=1, orders=(1,))
     tot_t, tot_n, desc, cores = 0.0, 0, "", 1
     for s in range(args.steps):
-        rate, dt, desc, cores = oracle_sample_rate(w, h, eri, ntup_per_order=1,
-                                                   orders=(1, 2, 3), seed=100 + s)
+        rate, dt, desc, cores, _ = oracle_sample_rate(w, h, eri, ntup_per_order=1,
+                                                      orders=(1, 2, 3), seed=100 + s)
         tot_t += dt
         tot_n += int(round(rate * dt))
     value = tot_n / tot_t
@@ -275,7 +294,7 @@ def main():
             t_last[0] = t
 
         return driver.run_expansion(m.ctx, w["ref"], w["exp"], max_order, w["thr"], rank, world,
-                                    allgather, callback=mark)
+                                    allgather, callback=mark, nocc=w["nocc"])
 
     def barrier():
         if world > 1:
@@ -327,6 +346,8 @@ def main():
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     pk, pk_kind = peaks()
+    # FP64 / FP32 FMA rates of this GPU, measured by the library's probe
+    fp_peaks = B.mbe_measure_peaks(local)
     if prec == B.MBE_FP64:
         dom_ms_per = st["fp64_ms"] / max(st["fp64_launches"], 1)
         dom_flops_per = st["fp64_flops"] / max(st["fp64_launches"], 1)
@@ -338,7 +359,8 @@ def main():
     achieved_tf = dom_flops_per / (dom_ms_per * 1e-3) / 1e12 if dom_ms_per > 0 else None
     if prec == B.MBE_FP64:
         kname = "k_contract_fp64"
-        peak_tf, peak_src = 1.25, "nominal GB300 FP64 1.25 TFLOP/s (no measured FP64 peak)"
+        peak_tf = fp_peaks["fp64_tflops"]
+        peak_src = "FP64 FMA, measured by mbe_measure_peaks on this GPU"
         bound = "alu"
         ksrc = "paper_1905_02786_gb300/csrc/mbe_ci.cu"
     else:
@@ -361,43 +383,65 @@ def main():
                 "kernel_ms_total": dom_ms_per * dom_launches, "step_ms_total": t_ms}
 
     # plain FP64 GPU path, one tuple at a time, vs the mixed batched path on
-    # the same bounded sample (orders 2-4 of the workload)
+    # the same bounded samples: seeded tuples of orders 5 and 6 (the orders
+    # that dominate the step; half of them with orbital 0, i.e. the 8-electron
+    # CASCIs) and of orders 2-4
     cmp = None
     if rank == 0 and not args.no_fp64_compare:
-        sample = {k: np.array(ms.sample_tuples(w["exp"], k, 8, 300 + k), dtype=np.int32)
-                  for k in (2, 3, 4)}
-        rates = {}
-        for label, opts in (("fp64_one_tuple", dict(precision=B.MBE_FP64, max_batch=1)),
-                            ("mixed_batched", dict(precision=B.MBE_MIXED_BF16X3,
-                                                   max_batch=args.max_batch))):
-            mm = B.MBE(local, timing=1, **opts)
-            mm.load(h, eri, w["nel"])
-            B.mbe_set_reference(mm.ctx, w["ref"], w["exp"])
-            B.mbe_reset_stats(mm.ctx)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            nt = 0
-            for k, tk in sample.items():
-                B.mbe_solve_tuples(mm.ctx, tk, k)
-                nt += len(tk)
-            torch.cuda.synchronize()
-            dt = time.perf_counter() - t0
-            s2 = B.mbe_get_stats(mm.ctx)
-            rates[label] = {"value": nt / dt, "unit": UNIT, "tuples": nt,
-                            "sigma_tflops_tensor_core": (s2["dom_flops"] / (s2["dom_ms"] * 1e-3)
-                                                         / 1e12) if s2["dom_ms"] else None,
-                            "sigma_tflops_fp64": (s2["fp64_flops"] / (s2["fp64_ms"] * 1e-3) / 1e12)
-                            if s2["fp64_ms"] else None}
-            mm.close()
-        rates["speedup"] = rates["mixed_batched"]["value"] / rates["fp64_one_tuple"]["value"]
-        rates["sample"] = "8 seeded random tuples each of orders 2, 3, 4 of " + args.workload
-        cmp = rates
+        rest = [o for o in w["exp"] if o != 0]
+
+        def high(k, n, seed):
+            with0 = [(0,) + t for t in ms.sample_tuples(rest, k - 1, n // 2, seed)]
+            return np.array(with0 + ms.sample_tuples(rest, k, n - n // 2, seed + 50),
+                            dtype=np.int32)
+
+        samples = {
+            "orders_5_6": ({5: high(5, 8, 501), 6: high(6, 8, 601)},
+                           "8 seeded tuples each of orders 5 and 6 (4 with orbital 0: 8e/11o "
+                           "and 8e/12o CASCIs; 4 without: 6e/11o and 6e/12o) of " + args.workload),
+            "orders_2_4": ({k: np.array(ms.sample_tuples(w["exp"], k, 8, 300 + k), dtype=np.int32)
+                            for k in (2, 3, 4)},
+                           "8 seeded random tuples each of orders 2, 3, 4 of " + args.workload)}
+        cmp = {}
+        for key, (sample, desc) in samples.items():
+            rates = {}
+            for label, opts in (("fp64_one_tuple", dict(precision=B.MBE_FP64, max_batch=1)),
+                                ("mixed_batched", dict(precision=B.MBE_MIXED_BF16X3,
+                                                       max_batch=args.max_batch))):
+                mm = B.MBE(local, timing=1, **opts)
+                mm.load(h, eri, w["nel"])
+                B.mbe_set_reference(mm.ctx, w["ref"], w["exp"])
+                B.mbe_reset_stats(mm.ctx)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                nt = 0
+                for k, tk in sample.items():
+                    B.mbe_solve_tuples(mm.ctx, tk, k)
+                    nt += len(tk)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                s2 = B.mbe_get_stats(mm.ctx)
+                rates[label] = {"value": nt / dt, "unit": UNIT, "tuples": nt,
+                                "sigma_tflops_tensor_core": (s2["dom_flops"] / (s2["dom_ms"] * 1e-3)
+                                                             / 1e12) if s2["dom_ms"] else None,
+                                "sigma_tflops_fp64": (s2["fp64_flops"] / (s2["fp64_ms"] * 1e-3)
+                                                      / 1e12) if s2["fp64_ms"] else None}
+                mm.close()
+            rates["speedup"] = rates["mixed_batched"]["value"] / rates["fp64_one_tuple"]["value"]
+            rates["sample"] = desc
+            cmp[key] = rates
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        rate, dt, desc, cores = oracle_sample_rate(w, h, eri)
+        rate, dt, desc, cores, sec = oracle_sample_rate(w, h, eri)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
-               "seconds": dt}
+               "seconds": dt, "oracle_seconds_per_casci_by_order": sec}
+        if args.workload == DEFAULT_WORKLOAD:
+            # the CASCIs that dominate the step are too large for the oracle's
+            # Davidson within the bench: one oracle sigma vector of an order-6
+            # 8e/12o CASCI is timed instead, beside the GPU's sigma vectors
+            sg_s, sg_ndet = oracle_sigma_seconds(w, h, eri, 6)
+            cpu["oracle_sigma_vector_s"] = {"order": 6, "ndet": sg_ndet, "seconds": sg_s}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -429,6 +473,7 @@ def main():
                 "seconds_per_order": list(order_s),
                 "noconv": st["noconv"],
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "measured_fp_peaks": fp_peaks,
                 "mixed_vs_fp64_gpu": cmp,
                 "gpu_launches": int(st["launches"]), "clocks": clk,
                 "total_energy": res["total"]}

@@ -52,7 +52,9 @@ enum {
   MBE_ECUDA = -3,     /* a CUDA runtime call failed                          */
   MBE_ENOCONV = -4,   /* some CASCI did not converge (see status_out)       */
   MBE_ELOOKUP = -5,   /* a subtuple increment was missing from the hash     */
-  MBE_ESTATE = -6     /* call out of sequence (e.g. no integrals loaded)    */
+  MBE_ESTATE = -6,    /* call out of sequence (e.g. no integrals loaded)    */
+  MBE_ETIMEOUT = -7   /* a bounded device-side wait gave up (opt.wait_limit);
+                         the kernel returned, the context stays usable      */
 };
 
 /* Precision of the sigma-vector contraction. */
@@ -123,6 +125,12 @@ typedef struct mbe_options {
                               Davidson correction (0 = diagonal only; at most
                               128; capped at half the symmetric space;
                               default 128)                                   */
+  int64_t wait_limit;      /* polls of an mbarrier a tensor-core kernel makes
+                              before it gives up, sets its error word and
+                              returns (the call then fails with MBE_ETIMEOUT);
+                              a poll lasts at most about a microsecond;
+                              default 2^24 (seconds); 0 gives up at the first
+                              wait (for tests of the error path)             */
 } mbe_options;
 
 typedef struct mbe_ctx mbe_ctx;
@@ -150,7 +158,7 @@ typedef struct mbe_stats {
 /* Fill *opt with the defaults (FP64, max_batch 256, subspace 20, 400
  * iterations, tol_r 1e-8, tol_e 1e-12, spin_shift 0.5, keep_ci 0,
  * deterministic 1, no memory cap, warm_start 0, mixed schedule 1e-5 / 1e-2 /
- * 2e-7, pspace 128). */
+ * 2e-7, pspace 128, wait_limit 2^24). */
 void mbe_default_options(mbe_options* opt);
 
 /* Create a context on CUDA device `device`.  opt may be NULL (defaults).
@@ -285,6 +293,15 @@ int mbe_sigma(mbe_ctx* ctx, const int* act, int nact, const double* c,
  * copies the core energy to the host and waits for the stream. */
 int mbe_sigma_noalloc(mbe_ctx* ctx, const int* act, int nact, const double* c_dev,
                       double* sigma_dev, int64_t ndet, double* e_core);
+
+/* Arithmetic peaks of CUDA device `device` measured by the library (no
+ * counterpart in the paper; a measurement aid for rooflines): FMA throughput
+ * of CUDA-core FP64 and FP32 arithmetic in TFLOP/s (2 flops per FMA), from
+ * probe kernels of independent FMA chains on 8 CTAs per SM timed with CUDA
+ * events (best of three launches after a warm-up).  Takes well under a
+ * second; allocates a small output buffer with cudaMalloc.
+ *  fp64_tflops, fp32_tflops  host outputs (either may be NULL) */
+int mbe_measure_peaks(int device, double* fp64_tflops, double* fp32_tflops);
 
 #ifdef __cplusplus
 }

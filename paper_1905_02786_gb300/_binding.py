@@ -15,17 +15,17 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_lib", "libmbe.so")
 
-MBE_OK, MBE_EINVAL, MBE_ENOMEM, MBE_ECUDA, MBE_ENOCONV, MBE_ELOOKUP, MBE_ESTATE = \
-    0, -1, -2, -3, -4, -5, -6
+MBE_OK, MBE_EINVAL, MBE_ENOMEM, MBE_ECUDA, MBE_ENOCONV, MBE_ELOOKUP, MBE_ESTATE, MBE_ETIMEOUT = \
+    0, -1, -2, -3, -4, -5, -6, -7
 MBE_FP64, MBE_MIXED_BF16X3, MBE_EMULATED_FP64 = 0, 1, 2
 ERROR_NAMES = {0: "MBE_OK", -1: "MBE_EINVAL", -2: "MBE_ENOMEM", -3: "MBE_ECUDA",
-               -4: "MBE_ENOCONV", -5: "MBE_ELOOKUP", -6: "MBE_ESTATE"}
+               -4: "MBE_ENOCONV", -5: "MBE_ELOOKUP", -6: "MBE_ESTATE", -7: "MBE_ETIMEOUT"}
 
 EXPORTED = ["mbe_default_options", "mbe_create", "mbe_destroy", "mbe_last_error",
             "mbe_load_integrals", "mbe_set_reference", "mbe_solve_tuples",
             "mbe_increments", "mbe_next_tuples", "mbe_energy_backward", "mbe_sigma",
             "mbe_get_stats", "mbe_reset_stats", "mbe_set_order_energies", "mbe_set_stream",
-            "mbe_sigma_noalloc"]
+            "mbe_sigma_noalloc", "mbe_measure_peaks"]
 
 
 class MBEError(RuntimeError):
@@ -43,7 +43,8 @@ class mbe_options(ctypes.Structure):
                 ("timing", ctypes.c_int), ("verbose", ctypes.c_int),
                 ("backward_share", ctypes.c_int), ("warm_start", ctypes.c_int),
                 ("mixed_stage_tol", ctypes.c_double), ("mixed_round_drop", ctypes.c_double),
-                ("mixed_rel_tol", ctypes.c_double), ("pspace", ctypes.c_int)]
+                ("mixed_rel_tol", ctypes.c_double), ("pspace", ctypes.c_int),
+                ("wait_limit", ctypes.c_int64)]
 
 
 _lib = None
@@ -74,6 +75,7 @@ def load_library(path: str = LIB_PATH):
     L.mbe_energy_backward.argtypes = [vp, c_double, vp, vp]
     L.mbe_sigma.argtypes = [vp, vp, c_int, vp, vp, vp]
     L.mbe_sigma_noalloc.argtypes = [vp, vp, c_int, vp, vp, ctypes.c_int64, vp]
+    L.mbe_measure_peaks.argtypes = [c_int, vp, vp]
     for name in EXPORTED:
         if name not in ("mbe_default_options", "mbe_destroy", "mbe_last_error",
                         "mbe_get_stats", "mbe_reset_stats", "mbe_set_order_energies",
@@ -298,3 +300,13 @@ def mbe_set_stream(ctx, stream_handle):
     L = load_library()
     L.mbe_set_stream.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
     _check(ctx, L.mbe_set_stream(ctx, ctypes.c_void_p(stream_handle or None)))
+
+
+def mbe_measure_peaks(device: int = 0) -> dict:
+    """FP64 and FP32 FMA peaks (TFLOP/s) of the device, measured by the
+    library's probe kernels."""
+    out = np.zeros(2)
+    rc = load_library().mbe_measure_peaks(int(device), _p(out[:1]), _p(out[1:]))
+    if rc != MBE_OK:
+        raise MBEError(rc, "mbe_measure_peaks failed")
+    return {"fp64_tflops": float(out[0]), "fp32_tflops": float(out[1])}

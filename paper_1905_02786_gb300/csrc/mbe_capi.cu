@@ -173,11 +173,12 @@ void solve_jobs(mbe_ctx* ctx, const std::vector<std::vector<int>>& acts, double*
     StringTables* tab = get_tables(ctx, n, nsig);
     const int64_t N = (int64_t)tab->nstr * tab->nstr;
     // device bytes per tuple: the mixed Davidson holds V and AV (M vectors
-    // each) and five work vectors in FP32 plus two FP64 exact-point vectors
-    // and the P-space eigenvectors; the FP64 one 2M + 6 FP64 vectors
+    // each) and five work vectors in FP32 plus two FP64 exact-point vectors,
+    // the bf16 hi/lo copies of the sigma operand and of H^alpha and the
+    // P-space eigenvectors; the FP64 one 2M + 6 FP64 vectors
     const bool mixed_bin = ctx->opt.precision == MBE_MIXED_BF16X3 && N > 1 &&
                            sigma_tc_supported(n, tab->nstr) && ozaki_supported(tab->npair);
-    double per = (mixed_bin ? (double)(8 * M + 36) * N + 128.0 * 129.0 * 4.0
+    double per = (mixed_bin ? (double)(8 * M + 46) * N + 128.0 * 129.0 * 4.0
                             : (double)(2 * M + 6) * N * 8.0) +
                  (double)tab->npair * tab->npair * 8.0 * 2.0;
     int64_t bmem = std::max<int64_t>(1, (int64_t)(budget / per));
@@ -297,6 +298,7 @@ void mbe_default_options(mbe_options* o) {
   o->mixed_round_drop = 1e-2;
   o->mixed_rel_tol = 2e-7;
   o->pspace = 128;
+  o->wait_limit = 1LL << 24;
 }
 
 int mbe_create(mbe_ctx** out, int device, const mbe_options* opt) {
@@ -311,7 +313,7 @@ int mbe_create(mbe_ctx** out, int device, const mbe_options* opt) {
   if (o.max_batch < 1 || o.max_subspace < 4 || o.max_subspace > 32 || o.max_iter < 1)
     return MBE_EINVAL;
   if (!(o.mixed_stage_tol > 0.0) || !(o.mixed_round_drop > 0.0 && o.mixed_round_drop < 1.0) ||
-      !(o.mixed_rel_tol > 0.0) || o.pspace < 0 || o.pspace > 128)
+      !(o.mixed_rel_tol > 0.0) || o.pspace < 0 || o.pspace > 128 || o.wait_limit < 0)
     return MBE_EINVAL;
   int ndev = 0;
   if (device < 0 || device >= MBE_MAX_DEVICES) return MBE_EINVAL;
@@ -743,7 +745,7 @@ int mbe_sigma(mbe_ctx* ctx, const int* act, int nact, const double* c, double* s
       CU_CHECK(cudaMemcpyAsync(cdf.ptr, cf.data(), sizeof(float) * bp.ndet, cudaMemcpyHostToDevice,
                                ctx->stream));
       sigma_tc(ctx, bp, w, cdf.ptr, bp.ndet, sdf.ptr, bp.ndet, nullptr, ctx->opt.spin_shift);
-      if (sigma_tc_error(ctx, w)) return fail(ctx, MBE_ECUDA, "tensor-core sigma wait timed out");
+      if (sigma_tc_error(ctx, w)) return fail(ctx, MBE_ETIMEOUT, "tensor-core sigma wait timed out");
       CU_CHECK(cudaMemcpyAsync(sf.data(), sdf.ptr, sizeof(float) * bp.ndet, cudaMemcpyDeviceToHost,
                                ctx->stream));
       double ec = 0.0;
@@ -774,12 +776,12 @@ int mbe_sigma(mbe_ctx* ctx, const int* act, int nact, const double* c, double* s
         sigma_exact(ctx, bp, w, cdf.ptr, bp.ndet, sd.ptr, bp.ndet, nullptr);
         launch_finish_sym_fp64(ctx, bp, sd.ptr, bp.ndet, cd.ptr, bp.ndet, ctx->opt.spin_shift,
                                nullptr);
-        if (sigma_tc_error(ctx, w)) return fail(ctx, MBE_ECUDA, "fused exact sigma wait timed out");
+        if (sigma_tc_error(ctx, w)) return fail(ctx, MBE_ETIMEOUT, "fused exact sigma wait timed out");
       } else {
         const bool emu = ctx->opt.precision == MBE_EMULATED_FP64 && ozaki_supported(bp.npair);
         sigma_fp64(ctx, bp, w, cd.ptr, bp.ndet, sd.ptr, bp.ndet, nullptr, ctx->opt.spin_shift, emu);
         if (emu && sigma_tc_error(ctx, w))
-          return fail(ctx, MBE_ECUDA, "tensor-core contraction wait timed out");
+          return fail(ctx, MBE_ETIMEOUT, "tensor-core contraction wait timed out");
       }
     }
     CU_CHECK(cudaMemcpyAsync(sigma, sd.ptr, sizeof(double) * bp.ndet, cudaMemcpyDeviceToHost,

@@ -530,7 +530,7 @@ void davidson_batch(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int32_t* s
 
   stage(false, ctx->opt.conv_tol_e, 0, 1, max_iter, B, false);
   if (emulated && sigma_tc_error(ctx, sw))
-    throw MbeError{MBE_ECUDA, "tensor-core contraction wait timed out"};
+    throw MbeError{MBE_ETIMEOUT, "tensor-core contraction wait timed out"};
 
   // status and energies: eps = E_core + theta - shift <x|S^2|x> / <x|x>
   std::vector<int32_t> it_h(B);

@@ -1023,7 +1023,7 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
     extend(1, true, false);
     stage(2, 40, 0, true, na);
   }
-  if (sigma_tc_error(ctx, sw)) throw MbeError{MBE_ECUDA, "tensor-core sigma wait timed out"};
+  if (sigma_tc_error(ctx, sw)) throw MbeError{MBE_ETIMEOUT, "tensor-core sigma wait timed out"};
 
   // energies: E = E_core + theta_x - shift <S^2> (S^2 of the exact-point vector, FP64)
   s2_apply(ctx, bp, C64.ptr, N, S64.ptr, N, nullptr);

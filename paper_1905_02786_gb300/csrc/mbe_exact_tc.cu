@@ -163,7 +163,8 @@ __global__ void __launch_bounds__(EX_THREADS, 1)
 k_sigma_exact(const int32_t* __restrict__ link, int nstr, int npair, int kpad,
               const uint8_t* __restrict__ gslices, const int32_t* __restrict__ ge,
               const float* __restrict__ c, int64_t c_stride, const int32_t* __restrict__ active,
-              double* __restrict__ X, int64_t x_stride, int32_t* __restrict__ err) {
+              double* __restrict__ X, int64_t x_stride, long long wait_limit,
+              int32_t* __restrict__ err) {
   constexpr int W = EX_M / R;
   const int LS = ex_link_stride(kpad);
   const int b = blockIdx.y;
@@ -331,10 +332,14 @@ k_sigma_exact(const int32_t* __restrict__ link, int nstr, int npair, int kpad,
       }
       mma_commit(&mbar);
     }
-    const int timed_out = mbar_wait(&mbar, phase) ? 0 : 1;
+    const int timed_out = mbar_wait(&mbar, phase, wait_limit) ? 0 : 1;
     if (__syncthreads_or(timed_out)) {
       ok = false;
-      if (tid == 0) atomicExch(err, MBE_ECUDA);
+      if (tid == 0) {
+        atomicExch(err, MBE_ETIMEOUT);
+        // the issued MMAs end before the accumulators are freed
+        mbar_wait(&mbar, phase, SPIN_LIMIT);
+      }
     }
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -431,11 +436,11 @@ void sigma_exact(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const float* c, int
   if (R == 2)
     k_sigma_exact<2><<<grid, EX_THREADS, L.total, ctx->stream>>>(
         bp.tab->link.ptr, nstr, npair, kpad, w.gex.ptr, w.gexp.ptr, c, c_stride, active, X,
-        x_stride, w.err.ptr);
+        x_stride, ctx->opt.wait_limit, w.err.ptr);
   else
     k_sigma_exact<1><<<grid, EX_THREADS, L.total, ctx->stream>>>(
         bp.tab->link.ptr, nstr, npair, kpad, w.gex.ptr, w.gexp.ptr, c, c_stride, active, X,
-        x_stride, w.err.ptr);
+        x_stride, ctx->opt.wait_limit, w.err.ptr);
   CU_LAUNCH_CHECK();
   ctx->fp64_timer.end(ctx->stream, ev);
   ctx->stats.fp64_launches += 1;

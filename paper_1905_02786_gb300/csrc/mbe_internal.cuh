@@ -128,6 +128,17 @@ struct StringTables {
   int n = 0, nsig = 0, nstr = 0, npair = 0;
   DevBuf<uint32_t> masks;  // nstr
   DevBuf<int32_t> link;    // nstr * npair
+  // the same links compacted per string (tensor-core sigma, built on first
+  // use): nlink = nsig (n - nsig + 1) entries (J << 8) | (P << 1) | (sign < 0)
+  // per string, ascending in P
+  DevBuf<int32_t> lnk;
+  int nlink = -1;
+  // for every string J its links ordered by the 128-string tile of the
+  // linked string, as offsets into the tensor-core sigma's staged tile
+  // (plist, int16 with the sign in bit 15) and the first entry of each tile
+  // (poff, ntiles + 1 per string)
+  DevBuf<int16_t> plist;
+  DevBuf<int32_t> poff;
 };
 
 // ------------------------------------------------------------- context
@@ -243,7 +254,8 @@ struct BinProblem {
   DevBuf<double> hp;             // B * n * n   (h' = heff - 1/2 sum_r (pr|rq))
   DevBuf<double> gp;             // B * npair * npair
   DevBuf<double> jk;             // B * 2 * n * n  (J_pq = (pp|qq), K_pq = (pq|qp))
-  DevBuf<uint8_t> gsplit;        // g' as bf16 hi/lo in the tensor-core operand layout
+  DevBuf<uint8_t> gsplit;        // g'/2 as bf16 hi/lo rows (tensor-core sigma operand source)
+  DevBuf<uint8_t> haa;           // one-spin Hamiltonian H^alpha as bf16 hi/lo rows
 };
 
 // P-space preconditioner of the mixed Davidson iteration (mbe_pspace.cu):
@@ -296,7 +308,8 @@ void launch_hdiag(mbe_ctx* ctx, BinProblem& bp, double spin_shift, double* hd);
 // strides (elements between consecutive tuples' vectors); active may be NULL.
 struct SigmaWork {
   DevBuf<double> D, E;           // scratch for the FP64 path
-  DevBuf<float> Xf;              // X rows of the tensor-core path (sigma = X + X^T)
+  DevBuf<float> Xf;              // W rows of the tensor-core path (sigma = W + W^T)
+  DevBuf<uint8_t> csplit;        // the vectors as bf16 hi/lo rows (tensor-core operands)
   DevBuf<int32_t> err;           // timeout flag of the tensor-core path
   DevBuf<uint8_t> gex;           // g' digit planes of the fused exact sigma
   DevBuf<int32_t> gexp;          // their row exponents

@@ -88,7 +88,8 @@ __host__ __device__ inline OzLayout oz_layout(int kpad) {
 __global__ void __launch_bounds__(OZ_THREADS, 1)
 k_contract_ozaki(const double* __restrict__ gp_all, int npair, int kpad,
                  const double* __restrict__ D, int64_t ndet, const int32_t* __restrict__ active,
-                 const int32_t* __restrict__ bmap, double* __restrict__ E, int32_t* __restrict__ err) {
+                 const int32_t* __restrict__ bmap, double* __restrict__ E, long long wait_limit,
+                 int32_t* __restrict__ err) {
   const int bl = blockIdx.y;
   const int b = bmap[bl];
   if (active && !active[b]) return;
@@ -212,12 +213,16 @@ k_contract_ozaki(const double* __restrict__ gp_all, int npair, int kpad,
                        smem_u32(&mbar))
                    : "memory");
     }
-    const int timed_out = mbar_wait(&mbar, phase) ? 0 : 1;
-    phase ^= 1u;
+    const int timed_out = mbar_wait(&mbar, phase, wait_limit) ? 0 : 1;
     if (__syncthreads_or(timed_out)) {
-      if (tid == 0) atomicExch(err, MBE_ECUDA);
+      if (tid == 0) {
+        atomicExch(err, MBE_ETIMEOUT);
+        // the issued MMAs end before the accumulators are freed
+        mbar_wait(&mbar, phase, SPIN_LIMIT);
+      }
       break;
     }
+    phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     // ---- epilogue: E = 2^(e_P + e_n - 54) I with the exact integer
     // I = sum_s acc_s 2^(8 (5 - s)) (|I| < 2^62).  Every acc_s is an exact
@@ -299,6 +304,6 @@ void contract_ozaki(mbe_ctx* ctx, const double* gp, int npair, const double* D, 
   per_tuple = std::max<int64_t>(per_tuple, (ntiles + 31) / 32);
   dim3 grid((unsigned)std::min<int64_t>(per_tuple, ntiles), nb);
   k_contract_ozaki<<<grid, OZ_THREADS, L.total, ctx->stream>>>(gp, npair, kpad, D, ndet, active,
-                                                                bmap, E, err);
+                                                                bmap, E, ctx->opt.wait_limit, err);
   CU_LAUNCH_CHECK();
 }

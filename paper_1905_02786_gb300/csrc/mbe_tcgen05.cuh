@@ -9,7 +9,7 @@
 
 namespace tc5 {
 
-constexpr long long SPIN_LIMIT = 1LL << 28;   // mbarrier polls before giving up
+constexpr long long SPIN_LIMIT = 1LL << 28;   // default mbarrier polls before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -38,6 +38,14 @@ __host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
 }
+// the same with A and B MN-major (bit 15: A transposed, bit 16: B
+// transposed).  An MN-major no-swizzle operand is a grid of core matrices of
+// 8 K-rows x 16 bytes (8 consecutive M or N elements); the descriptor's SBO
+// is the byte stride between core matrices adjacent in M (or N), its LBO the
+// stride between core matrices adjacent in K.
+__host__ __device__ constexpr uint32_t make_idesc_mn(int M, int N) {
+  return make_idesc(M, N) | (1u << 15) | (1u << 16);
+}
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
                                          uint32_t accumulate) {
@@ -58,21 +66,83 @@ __device__ __forceinline__ void mbar_init(uint64_t* mbar, int count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count));
 }
 
-// bounded wait on an mbarrier phase; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t phase) {
+__device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t phase) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(done)
+      : "r"(addr), "r"(phase)
+      : "memory");
+  return done != 0;
+}
+
+// bounded wait on an mbarrier phase (at most `limit` polls); false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t phase,
+                                          long long limit = SPIN_LIMIT) {
   const uint32_t addr = smem_u32(mbar);
-  for (long long i = 0; i < SPIN_LIMIT; i++) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done)
-        : "r"(addr), "r"(phase)
-        : "memory");
-    if (done) return true;
+  for (long long i = 0; i < limit; i++)
+    if (mbar_try(addr, phase)) return true;
+  return false;
+}
+
+// try_wait with a suspend-time hint: the thread may sleep until the phase
+// completes or about hint_ns nanoseconds have passed, instead of spinning
+__device__ __forceinline__ bool mbar_try_hint(uint32_t addr, uint32_t phase, uint32_t hint_ns) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(done)
+      : "r"(addr), "r"(phase), "r"(hint_ns)
+      : "memory");
+  return done != 0;
+}
+
+// bounded wait (at most `limit` polls, each suspending up to hint_ns) that
+// also gives up once another role of the CTA has set *abort (checked every
+// 16 polls); after 4 failed polls the thread sleeps between polls (32 ns,
+// doubling up to max_sleep_ns) so that a waiting role leaves the issue slots
+// to the working ones; false on timeout or abort
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* mbar, uint32_t phase, long long limit,
+                                                   const volatile int* abort,
+                                                   uint32_t hint_ns = 0,
+                                                   uint32_t max_sleep_ns = 0) {
+  const uint32_t addr = smem_u32(mbar);
+  uint32_t ns = 32;
+  for (long long i = 0; i < limit; i++) {
+    if (hint_ns ? mbar_try_hint(addr, phase, hint_ns) : mbar_try(addr, phase)) return true;
+    if ((i & 15) == 15 && *abort) return false;
+    if (max_sleep_ns && i >= 3) {
+      __nanosleep(ns);
+      ns = ns < max_sleep_ns ? 2 * ns : max_sleep_ns;
+    }
   }
   return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
+}
+
+// 16-byte asynchronous global -> shared copy; src_bytes 0 writes zeros
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+               "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
@@ -99,6 +169,25 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// 4 columns, no wait
+__device__ __forceinline__ void tmem_ld4_nowait(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+}
+
+// 8 columns, no wait (several loads then one tmem_wait_ld)
+__device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 // two 8-column loads (columns at taddr0 and taddr1) under one wait; the

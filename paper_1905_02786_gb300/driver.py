@@ -2,30 +2,62 @@
 
 The tuples of one order are independent CASCI problems (Sec. 2; the paper
 farms them out to MPI workers, Sec. 4.2.3).  With ``world > 1`` every
-process generates the same order-k tuple list on its GPU, solves the tuples
-i with i % world == rank, the energies are all-gathered (the one exchange
-per order), and every process then assembles the increments of the whole
-order (Eq. 3) so that all hashes stay identical for the next order.
+process generates the same order-k tuple list on its GPU, solves its share
+of the tuples, the energies are all-gathered (the one exchange per order),
+and every process then assembles the increments of the whole order (Eq. 3)
+so that all hashes stay identical for the next order.
+
+Shares: with per-tuple work estimates (the determinant count of the tuple's
+CASCI, which sets the cost of its sigma vectors; the iteration counts are
+alike) the tuples are dealt heaviest first to the least loaded rank, so the
+ranks carry equal work and each holds a share of every bin of equal size;
+without them, round-robin in lexicographic order.
 """
 from __future__ import annotations
+
+import math
 
 import numpy as np
 
 from . import _binding as B
 
 
-def shard_indices(n: int, rank: int, world: int) -> np.ndarray:
-    """Round-robin share of rank: tuples of similar size are interleaved in
-    lexicographic order, so every rank gets a similar mix."""
-    return np.arange(rank, n, world, dtype=np.int64)
+def shard_indices(n: int, rank: int, world: int, weights=None) -> np.ndarray:
+    """Indices (ascending) of the tuples that rank solves.  Deterministic:
+    every rank computes the same assignment from the same inputs."""
+    if weights is None or world == 1:
+        return np.arange(rank, n, world, dtype=np.int64)
+    return np.flatnonzero(shard_owner(np.asarray(weights, dtype=np.float64), world) == rank)
 
 
-def merge_shards(parts, n: int, world: int) -> np.ndarray:
+def shard_owner(weights: np.ndarray, world: int) -> np.ndarray:
+    """Owner rank of every tuple: heaviest first (stable), each to the rank
+    with the least load so far (lowest rank on ties)."""
+    order = np.argsort(-weights, kind="stable")
+    load = np.zeros(world)
+    owner = np.empty(len(weights), dtype=np.int64)
+    for i in order:
+        r = int(np.argmin(load))
+        owner[i] = r
+        load[r] += weights[i]
+    return owner
+
+
+def merge_shards(parts, n: int, world: int, weights=None) -> np.ndarray:
     """Inverse of shard_indices: parts[r] holds the values of rank r's share."""
     out = np.empty(n)
     for r in range(world):
-        out[shard_indices(n, r, world)] = parts[r]
+        out[shard_indices(n, r, world, weights)] = parts[r]
     return out
+
+
+def tuple_weights(tuples: np.ndarray, ref, nocc: int) -> np.ndarray:
+    """Work estimate of each tuple's CASCI: its determinant count C(n, n_sigma)^2,
+    n = |Pi| + order active orbitals, n_sigma = occupied orbitals among them."""
+    n = len(ref) + tuples.shape[1]
+    ns_ref = sum(1 for r in ref if r < nocc)
+    ns = ns_ref + (tuples < nocc).sum(axis=1)
+    return np.array([float(math.comb(n, int(s))) ** 2 for s in ns])
 
 
 def torch_allgather(group=None):
@@ -61,13 +93,14 @@ def torch_allreduce_sum(group=None):
 
 
 def run_expansion(ctx, ref, exp, max_order, thr=0.0, rank=0, world=1, allgather=None,
-                  solve=None, callback=None, api=None):
+                  solve=None, callback=None, api=None, nocc=None):
     """Run orders 1..max_order; returns dict(eps_ref, orders, total, ntup).
 
     ``api`` is the module of C-ABI wrappers (default: the binding);
     ``solve(ctx, tuples, k) -> eps`` defaults to its mbe_solve_tuples.  Tests
     pass a host stand-in for both to exercise the sharding logic without a
-    GPU."""
+    GPU.  With ``nocc`` (occupied orbitals of the reference determinant) the
+    shares are weighted by the tuples' determinant counts."""
     B_ = api or B
     if solve is None:
         def solve(c, t, k):
@@ -81,11 +114,13 @@ def run_expansion(ctx, ref, exp, max_order, thr=0.0, rank=0, world=1, allgather=
         n = len(tuples)
         if n == 0:
             break
-        mine = shard_indices(n, rank, world)
+        wts = tuple_weights(tuples, ref, nocc) if (nocc is not None and world > 1) else None
+        mine = shard_indices(n, rank, world, wts)
         eps_local = solve(ctx, tuples[mine], k) if len(mine) else np.zeros(0)
         if world > 1:
-            counts = [len(shard_indices(n, r, world)) for r in range(world)]
-            eps = merge_shards(allgather(np.asarray(eps_local, dtype=np.float64), counts), n, world)
+            counts = [len(shard_indices(n, r, world, wts)) for r in range(world)]
+            eps = merge_shards(allgather(np.asarray(eps_local, dtype=np.float64), counts), n,
+                               world, wts)
             B_.mbe_set_order_energies(ctx, tuples, eps, k)
         else:
             eps = eps_local

@@ -9,6 +9,7 @@ the sharding logic itself runs without a GPU.
 """
 import multiprocessing as mp
 import os
+import math
 import socket
 
 import numpy as np
@@ -93,7 +94,7 @@ def _worker(rank, world, port, q):
         h, eri, _ = ms.gen_integrals(NORB, NOCC, SEED)
         api = HostAPI(h, eri, NOCC, share=2 if rank == 0 else 1)
         res = driver.run_expansion(None, REF, EXP, MAX_ORDER, THR, rank=rank, world=world,
-                                   allgather=driver.torch_allgather(), api=api)
+                                   allgather=driver.torch_allgather(), api=api, nocc=NOCC)
         dh, dg = driver.sharded_backward(None, NORB, rank, world,
                                          driver.torch_allreduce_sum(), api=api)
         q.put((rank, res["total"], res["ntup"], len(api.held), dh, dg))
@@ -109,12 +110,29 @@ def _free_port():
 
 def test_shard_indices_partition():
     from paper_1905_02786_gb300 import driver
-    for n in (0, 1, 5, 17):
+    rng = np.random.default_rng(3)
+    for n in (0, 1, 5, 17, 200):
         for world in (1, 2, 3, 8):
-            parts = [driver.shard_indices(n, r, world) for r in range(world)]
-            assert sorted(np.concatenate(parts).tolist()) == list(range(n))
-            vals = np.arange(n, dtype=np.float64) * 1.5
-            assert np.array_equal(driver.merge_shards([vals[p] for p in parts], n, world), vals)
+            for weights in (None, rng.choice([48400.0, 245025.0, 108900.0], size=n)):
+                parts = [driver.shard_indices(n, r, world, weights) for r in range(world)]
+                assert sorted(np.concatenate(parts).tolist()) == list(range(n))
+                vals = np.arange(n, dtype=np.float64) * 1.5
+                got = driver.merge_shards([vals[p] for p in parts], n, world, weights)
+                assert np.array_equal(got, vals)
+                if weights is not None and n:
+                    # greedy heaviest-first: loads differ by at most one tuple's weight
+                    loads = [weights[p].sum() for p in parts]
+                    assert max(loads) - min(loads) <= weights.max()
+
+
+def test_tuple_weights_are_determinant_counts():
+    """The work estimate of a tuple is the determinant count of its CASCI:
+    Pi = {1..6} with orbitals 0-3 occupied (CAS(6e,6o)); adding occupied
+    orbital 0 gives 8 electrons, a virtual keeps 6."""
+    from paper_1905_02786_gb300 import driver
+    t = np.array([[0, 7, 8], [7, 8, 9]], dtype=np.int32)
+    w = driver.tuple_weights(t, [1, 2, 3, 4, 5, 6], 4)
+    assert w[0] == float(math.comb(9, 4)) ** 2 and w[1] == float(math.comb(9, 3)) ** 2
 
 
 @pytest.mark.timeout(600)
@@ -137,8 +155,8 @@ def test_sharded_expansion_gloo_world2():
         # every rank assembles the same total from the gathered energies
         assert abs(total - ref["total"]) < 1e-12
         assert nt == ntup
-        # round-robin: each rank solved about half of the tuples
-        assert abs(held - ntup / 2) <= MAX_ORDER
+        # shares weighted by determinant counts: each rank solved a part
+        assert 0 < held < ntup
         # the summed shares are the whole gradient
         assert np.max(np.abs(dh - odh)) < 1e-12
         assert np.max(np.abs(dg - odg)) < 1e-12

@@ -101,14 +101,15 @@ def test_missing_subtuple_is_elookup(lib, system):
 def test_memory_cap_is_enomem(lib, system, precision):
     w, h, eri, exp = system
     prec = lib.MBE_FP64 if precision == "fp64" else lib.MBE_MIXED_BF16X3
-    # 8e/12o CASCIs (245,025 determinants): the Davidson subspace alone is
-    # tens of MB, far above a 4 MB cap
-    tuples = np.array([(0, 7, 8, 9, 10, 11)], dtype=np.int32)
+    # with orbital 3 as the reference this tuple makes an 8e/12o CASCI
+    # (245,025 determinants): its Davidson subspace alone is tens of MB, far
+    # above a 4 MB cap
+    tuples = np.array([(0, 1, 2, 7, 8, 9, 10, 11, 12, 13, 14)], dtype=np.int32)
     m = lib.MBE(0, precision=prec, mem_cap_bytes=4 << 20)
     m.load(h, eri, w["nel"])
     lib.mbe_set_reference(m.ctx, REF, exp)
     with pytest.raises(lib.MBEError) as ei:
-        lib.mbe_solve_tuples(m.ctx, tuples, 6)
+        lib.mbe_solve_tuples(m.ctx, tuples, 11)
     assert ei.value.code == lib.MBE_ENOMEM
     m.close()
     _ok = lib.MBE(0, precision=prec)
@@ -118,3 +119,30 @@ def test_memory_cap_is_enomem(lib, system, precision):
     _ok.close()
     assert np.all(st == 0)
     assert abs(eps[0] - _oracle(w, h, eri, (0, 7))) < 1e-8
+
+
+def test_bounded_wait_gives_up_with_etimeout(lib):
+    """With a wait limit of zero polls the first mbarrier wait of the
+    tensor-core sigma gives up at once: its kernels set their error word,
+    wait for any MMA they issued, free their tensor memory and return; the
+    call fails with MBE_ETIMEOUT and the process goes on to compute the same
+    sigma correctly (no trap, no device fault)."""
+    norb, nocc, seed = 14, 4, 2
+    act = list(range(12))                             # 8e/12o, 495 strings
+    h, eri, _ = ms.gen_integrals(norb, nocc, seed)
+    c = ms.random_symmetric_ci(495, 3)[0]
+    m = lib.MBE(0, precision=lib.MBE_MIXED_BF16X3, wait_limit=0)
+    m.load(h, eri, 2 * nocc)
+    with pytest.raises(lib.MBEError) as ei:
+        lib.mbe_sigma(m.ctx, act, c)
+    assert ei.value.code == lib.MBE_ETIMEOUT
+    assert "timed out" in lib.mbe_last_error(m.ctx)
+    m.close()
+    sig = {}
+    for prec in (lib.MBE_MIXED_BF16X3, lib.MBE_FP64):
+        m = lib.MBE(0, precision=prec)
+        m.load(h, eri, 2 * nocc)
+        sig[prec], _ = lib.mbe_sigma(m.ctx, act, c)
+        m.close()
+    ref = sig[lib.MBE_FP64]
+    assert np.abs(sig[lib.MBE_MIXED_BF16X3] - ref).max() <= 2e-4 * np.abs(ref).max()

@@ -90,6 +90,7 @@ def test_mixed_sigma_sampled_rows_vs_oracle(lib, name, nstr):
     ref = ref - ecore * crow
     scale = np.abs(ref).max()
     err = np.abs(sig[rows] - ref).max()
+    print(f"\n[parity] mixed sigma {name}: max error / max element = {err / scale:.3e}")
     assert err <= 2e-4 * scale, (name, err, scale)
     s2 = sig.reshape(nstr, nstr)
     assert np.array_equal(s2, s2.T)
@@ -113,6 +114,7 @@ def test_exact_point_sigma_sampled_rows_vs_oracle(lib, name, nstr):
     ref = ref - ecore * crow
     scale = np.abs(ref).max()
     err = np.abs(sig[rows] - ref).max()
+    print(f"\n[parity] exact-point sigma {name}: max error / max element = {err / scale:.3e}")
     assert err <= 1e-9 * scale, (name, err, scale)
 
 
@@ -138,14 +140,17 @@ def test_mixed_energies_order5_order6_vs_oracle(lib):
     e_ref = lib.mbe_set_reference(m.ctx, w["ref"], w["exp"])
     assert abs(e_ref - gold[0][0][1]) < 1e-8
     nel = set()
+    worst = 0.0
     for order in (5, 6):
         tuples = [t for t, _ in gold[order]]
         eps, st = lib.mbe_solve_tuples(m.ctx, np.array(tuples, dtype=np.int32), order)
         assert np.all(st == 0)
         for (t, e_or), e in zip(gold[order], eps):
             assert abs(e - e_or) < 1e-8, (order, t, e, e_or)
+            worst = max(worst, abs(e - e_or))
             nel.add((order, 0 in t))
     m.close()
+    print(f"\n[parity] mixed CASCI energies, orders 5-6 of 8e/23o: max |E - E_oracle| = {worst:.3e} Eh")
     assert nel == {(5, True), (5, False), (6, True), (6, False)}
 
 
@@ -162,6 +167,7 @@ def test_allorder_fci8e12o_mixed_matches_golden(lib):
     # increments of the stored energies by the oracle's Moebius form of Eq. 3
     eps_o = {t: e for t, e in gold.items() if t}
     n = 0
+    we = wd = 0.0
     for o in res["orders"]:
         assert np.all(o["status"] == 0)
         for t, e, d in zip(o["tuples"], o["eps"], o["inc"]):
@@ -169,7 +175,11 @@ def test_allorder_fci8e12o_mixed_matches_golden(lib):
             assert abs(e - gold[key]) < 1e-8, (key, e, gold[key])
             d_o = om.increment_mobius(key, eps_o, gold[()])
             assert abs(d - d_o) < 1e-7, (key, d, d_o)
+            we, wd = max(we, abs(e - gold[key])), max(wd, abs(d - d_o))
             n += 1
+    print(f"\n[parity] mixed all-order 8e/12o: max |E - E_oracle| = {we:.3e} Eh, "
+          f"max |increment - oracle| = {wd:.3e} Eh, |total - FCI| = "
+          f"{abs(res['total'] - gold[tuple(w['exp'])]):.3e} Eh")
     assert n == 255
     assert abs(res["total"] - total) < 1e-7
     assert abs(res["total"] - gold[tuple(w["exp"])]) < 1e-7     # = full 8e/12o FCI
