@@ -37,13 +37,16 @@ METRIC = ("CASCI increments/sec and sigma TFLOP/s, mixed+batched vs plain FP64 G
 UNIT = "increments/s"
 DEFAULT_WORKLOAD = "h2o_dz_8e23o"
 
-# DRAM traffic per launch of the dominant kernel from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by kernel; valid only
-# while the kernel source is unchanged (sha256 of the source file).
-# ncu capture (profiles/k_sigma_tc_8e12o_batch64.md): dram__bytes_read.sum +
-# dram__bytes_write.sum of one k_sigma_tc launch over 64 active 8e/12o
-# tuples (2 N_det npair^2 = 1.9081e+11 flop), per algorithmic flop
-TRAFFIC = {"k_sigma_tc": {"bytes_per_flop": 4.666351e-04, "sha": "c5facf0329642a90"}}
+# DRAM traffic per launch of the dominant kernels from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), per algorithmic flop
+# (2 N_det npair^2 per sigma vector), keyed by kernel; valid only while the
+# kernel definition is unchanged (sha256 prefix of its source text).  From
+# the captures of one launch over 64 active 8e/12o tuples (1.9081e+11 flop),
+# profiles/k_sigma_ab_8e12o_batch64.md.
+TRAFFIC = {"k_gemm_haa": {"bytes_per_flop": (125788672 + 37701376) / 1.9081e11,
+                          "sha": "fc8f06c321a2b658"},
+           "k_sigma_ab": {"bytes_per_flop": (127396864 + 23573760) / 1.9081e11,
+                          "sha": "e602a005659bd9da"}}
 
 
 def peaks():
@@ -364,17 +367,24 @@ def main():
         bound = "alu"
         ksrc = "paper_1905_02786_gb300/csrc/mbe_ci.cu"
     else:
-        kname = "k_sigma_tc"
+        # the sigma contraction: k_gemm_haa (one-spin part) + k_sigma_ab
+        # (two-spin part), timed together with CUDA events on the library's
+        # stream; algorithmic flops 2 N_det npair^2 per sigma vector
+        kname = "k_gemm_haa+k_sigma_ab"
         peak_tf = pk.get("bf16_tflops_sustained", 1700.0)
         peak_src = f"bf16 dense sustained, {pk_kind}"
         bound = "tensor"
         ksrc = "paper_1905_02786_gb300/csrc/mbe_sigma_tc.cu"
-    # DRAM bytes per algorithmic flop from one ncu capture of the kernel
+    # DRAM bytes per algorithmic flop from one ncu capture of the kernels
     # (8e/12o batch of 64 tuples, bench --profile-batch 64), scaled to this
-    # run's average launch; null once the kernel source has changed
-    tr = TRAFFIC.get(kname)
-    traffic = (tr["bytes_per_flop"] * dom_flops_per
-               if tr and tr["sha"] == src_sha(ksrc, kname) else None)
+    # run's average launch; null once a kernel source has changed
+    traffic = 0.0
+    for kn in kname.split("+"):
+        tr = TRAFFIC.get(kn)
+        if not tr or tr["sha"] != src_sha(ksrc, kn):
+            traffic = None
+            break
+        traffic += tr["bytes_per_flop"] * dom_flops_per
     roofline = {"bound": bound, "kernel": kname, "achieved": achieved_tf, "peak": peak_tf,
                 "unit": "TFLOP/s", "frac": (achieved_tf / peak_tf) if achieved_tf else None,
                 "traffic": traffic, "peak_source": peak_src,

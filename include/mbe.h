@@ -223,6 +223,21 @@ int mbe_increments(mbe_ctx* ctx, int order, double screen_thr, double* inc_out,
 int mbe_next_tuples(mbe_ctx* ctx, int order, int32_t* tuples_out, int64_t cap,
                     int64_t* ntup_out);
 
+/* pi-pruning (Sec. 3): restrict the expansion to tuples that hold both
+ * orbitals of a given degenerate pair or neither.  The expansion then runs
+ * over units (single orbitals and pairs): mbe_next_tuples forms a tuple of
+ * order k (its orbital count) from a tuple with one unit fewer (order k-1 or
+ * k-2; the empty tuple for a lone unit) by the screening rule applied to its
+ * one-unit-removed subtuples, mbe_increments subtracts the increments of its
+ * proper non-empty sub-unions of units (Eq. 3 over units) and the MBE
+ * coefficients of mbe_energy_backward count units.  An order can be empty
+ * while the next one is not (a pair adds two orbitals).
+ *  pairs[2*npairs]  pairs of expansion orbitals (host); each orbital in at
+ *                   most one pair; npairs = 0 switches pruning off
+ * Call after mbe_set_reference and before the first order (MBE_ESTATE
+ * otherwise); mbe_set_reference switches pruning off. */
+int mbe_set_pruning_pairs(mbe_ctx* ctx, const int32_t* pairs, int npairs);
+
 /* Gradient of the MBE energy (eps_Pi + all increments processed so far)
  * with respect to the integrals, by Hellmann-Feynman: each CASCI energy is
  * stationary in its CI coefficients, so dE/dh_pq = sum_T c_T gamma^T_pq and

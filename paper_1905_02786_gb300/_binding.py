@@ -25,7 +25,7 @@ EXPORTED = ["mbe_default_options", "mbe_create", "mbe_destroy", "mbe_last_error"
             "mbe_load_integrals", "mbe_set_reference", "mbe_solve_tuples",
             "mbe_increments", "mbe_next_tuples", "mbe_energy_backward", "mbe_sigma",
             "mbe_get_stats", "mbe_reset_stats", "mbe_set_order_energies", "mbe_set_stream",
-            "mbe_sigma_noalloc", "mbe_measure_peaks"]
+            "mbe_sigma_noalloc", "mbe_measure_peaks", "mbe_set_pruning_pairs"]
 
 
 class MBEError(RuntimeError):
@@ -76,6 +76,7 @@ def load_library(path: str = LIB_PATH):
     L.mbe_sigma.argtypes = [vp, vp, c_int, vp, vp, vp]
     L.mbe_sigma_noalloc.argtypes = [vp, vp, c_int, vp, vp, ctypes.c_int64, vp]
     L.mbe_measure_peaks.argtypes = [c_int, vp, vp]
+    L.mbe_set_pruning_pairs.argtypes = [vp, vp, c_int]
     for name in EXPORTED:
         if name not in ("mbe_default_options", "mbe_destroy", "mbe_last_error",
                         "mbe_get_stats", "mbe_reset_stats", "mbe_set_order_energies",
@@ -235,16 +236,26 @@ class MBE:
         mbe_load_integrals(self.ctx, h, eri, nelec)
         self.norb = h.shape[0]
 
-    def run(self, ref, exp, max_order, thr=0.0, callback=None):
-        """Full expansion; returns dict(eps_ref, orders=[...], total)."""
+    def run(self, ref, exp, max_order, thr=0.0, callback=None, pairs=None):
+        """Full expansion (pi-pruned over ``pairs`` if given); returns
+        dict(eps_ref, orders=[...], total)."""
         e_ref = mbe_set_reference(self.ctx, ref, exp)
+        if pairs:
+            mbe_set_pruning_pairs(self.ctx, pairs)
         orders = []
         total = e_ref
+        empty_run = 0
         for k in range(1, max_order + 1):
             tuples = mbe_next_tuples(self.ctx, k)
             if len(tuples) == 0:
-                break
-            eps, st = mbe_solve_tuples(self.ctx, tuples, k)
+                # a pair adds two orbitals: with pruning an empty order can
+                # precede a non-empty one, two empty orders end the expansion
+                empty_run += 1
+                if empty_run >= (2 if pairs else 1):
+                    break
+            else:
+                empty_run = 0
+            eps, st = mbe_solve_tuples(self.ctx, tuples.reshape(-1, k), k)
             inc, keep, e_order, total = mbe_increments(self.ctx, k, thr, len(tuples))
             rec = dict(order=k, tuples=tuples, eps=eps, status=st, inc=inc, keep=keep,
                        E_order=e_order)
@@ -310,3 +321,10 @@ def mbe_measure_peaks(device: int = 0) -> dict:
     if rc != MBE_OK:
         raise MBEError(rc, "mbe_measure_peaks failed")
     return {"fp64_tflops": float(out[0]), "fp32_tflops": float(out[1])}
+
+
+def mbe_set_pruning_pairs(ctx, pairs):
+    """pi-pruning over pairs of degenerate expansion orbitals (Sec. 3)."""
+    pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    return _check(ctx, load_library().mbe_set_pruning_pairs(ctx, _p(pr) if pr.size else None,
+                                                            pr.shape[0]))

@@ -456,6 +456,8 @@ int mbe_set_reference(mbe_ctx* ctx, const int* ref_orbs, int nref, const int* ex
     ctx->prev_tuples.clear();
     ctx->prev_keep.clear();
     ctx->prev_order = 0;
+    ctx->pruned = false;
+    ctx->partner.assign(ctx->norb, -1);
     if (e_ref) *e_ref = e;
     if (st != MBE_OK) return fail(ctx, MBE_ENOCONV, "reference CASCI did not converge");
     return MBE_OK;
@@ -593,10 +595,47 @@ int mbe_increments(mbe_ctx* ctx, int order, double screen_thr, double* inc_out, 
   });
 }
 
+int mbe_set_pruning_pairs(mbe_ctx* ctx, const int32_t* pairs, int npairs) {
+  return guarded(ctx, [&]() -> int {
+    if (!ctx->have_ref) return fail(ctx, MBE_ESTATE, "no reference space set");
+    if (ctx->last_order != 0 || ctx->cur_order != 0)
+      return fail(ctx, MBE_ESTATE, "pruning pairs must be set before the first order");
+    if (npairs < 0 || (npairs && !pairs)) return fail(ctx, MBE_EINVAL, "bad pair arguments");
+    std::vector<int32_t> part(ctx->norb, -1);
+    std::set<int> expset(ctx->exp.begin(), ctx->exp.end());
+    for (int i = 0; i < npairs; i++) {
+      const int a = pairs[2 * i], b = pairs[2 * i + 1];
+      if (a == b || !expset.count(a) || !expset.count(b) || part[a] >= 0 || part[b] >= 0)
+        return fail(ctx, MBE_EINVAL, "pairs must join two distinct expansion orbitals, each once");
+      part[a] = b;
+      part[b] = a;
+    }
+    ctx->partner = part;
+    ctx->pruned = npairs > 0;
+    ctx->partner_dev.reset(&ctx->pool, std::max(1, ctx->norb));
+    CU_CHECK(cudaMemcpyAsync(ctx->partner_dev.ptr, part.data(), sizeof(int32_t) * ctx->norb,
+                             cudaMemcpyHostToDevice, ctx->stream));
+    CU_CHECK(cudaStreamSynchronize(ctx->stream));
+    return MBE_OK;
+  });
+}
+
 int mbe_next_tuples(mbe_ctx* ctx, int order, int32_t* tuples_out, int64_t cap, int64_t* ntup_out) {
   return guarded(ctx, [&]() -> int {
     if (!ctx->have_ref) return fail(ctx, MBE_ESTATE, "no reference space set");
     if (!ntup_out) return fail(ctx, MBE_EINVAL, "null ntup_out");
+    if (ctx->pruned) {
+      if (order < 1 || order > MBE_MAX_ORDER || order != ctx->last_order + 1)
+        return fail(ctx, MBE_ESTATE, "next tuples need the increments of order-1");
+      std::vector<int32_t> t = next_tuples_pruned(ctx, order);
+      const int64_t n = (int64_t)t.size() / order;
+      *ntup_out = n;
+      if (tuples_out) {
+        if (cap < n) return fail(ctx, MBE_EINVAL, "output capacity too small");
+        std::copy(t.begin(), t.end(), tuples_out);
+      }
+      return MBE_OK;
+    }
     if (order == 1) {
       int64_t n = (int64_t)ctx->exp.size();
       *ntup_out = n;

@@ -65,20 +65,51 @@ __global__ void k_hash_insert(unsigned long long* keys, double* val, uint8_t* ke
   atomicExch(err, MBE_ENOMEM);
 }
 
+// pi-pruning: for position i of a tuple, the bit of its partner's position
+// (0 for an orbital without partner); a subset m of the positions is a union
+// of units iff it holds the partner of each of its members
+__device__ __forceinline__ void partner_bits(const int* orb, int order,
+                                             const int32_t* __restrict__ partner, unsigned* pb) {
+  for (int i = 0; i < order; i++) {
+    pb[i] = 0u;
+    if (!partner) continue;
+    const int p = partner[orb[i]];
+    for (int j = 0; j < order; j++)
+      if (orb[j] == p) pb[i] = 1u << j;
+  }
+}
+__device__ __forceinline__ bool unit_closed(unsigned m, const unsigned* pb, int order) {
+  unsigned need = 0u;
+  for (int i = 0; i < order; i++)
+    if ((m >> i) & 1u) need |= pb[i];
+  return (need & ~m) == 0u;
+}
+// number of units in a unit-closed subset: each pair counted once
+__device__ __forceinline__ int unit_count(unsigned m, const unsigned* pb, int order) {
+  int n = 0;
+  for (int i = 0; i < order; i++)
+    if (((m >> i) & 1u) && (pb[i] == 0u || pb[i] > (1u << i))) n++;
+  return n;
+}
+
 // Eq. 3: inc_T = eps_T - eps_Pi - sum over proper non-empty subtuples S of
-// inc_S (all looked up in the hash).  Compensated summation, subsets visited
-// in increasing bit-mask order.
+// inc_S (all looked up in the hash); with pi-pruning (partner != NULL) over
+// the proper non-empty unions of units.  Compensated summation, subsets
+// visited in increasing bit-mask order.
 __global__ void k_increments(DevHash h, const int32_t* __restrict__ tuples, int order, int64_t ntup,
                              const double* __restrict__ eps, double eps_ref, double thr,
-                             double* __restrict__ inc, uint8_t* __restrict__ keep_out,
-                             int32_t* err) {
+                             const int32_t* __restrict__ partner, double* __restrict__ inc,
+                             uint8_t* __restrict__ keep_out, int32_t* err) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= ntup) return;
   int orb[MBE_MAX_ORDER];
+  unsigned pb[MBE_MAX_ORDER];
   for (int i = 0; i < order; i++) orb[i] = tuples[t * order + i];
+  partner_bits(orb, order, partner, pb);
   double s = eps[t] - eps_ref, comp = 0.0;
   const unsigned full = (1u << order) - 1u;
   for (unsigned m = 1; m < full; m++) {
+    if (partner && !unit_closed(m, pb, order)) continue;
     unsigned long long k0 = 0, k1 = 0;
     for (int i = 0; i < order; i++)
       if ((m >> i) & 1u) {
@@ -215,15 +246,21 @@ __global__ void k_gen_write(DevHash h, const int32_t* __restrict__ parents, int 
 // MBE coefficient of every processed tuple (Moebius inversion of Eq. 3):
 // each tuple T adds (-1)^(|T| - |S|) to the coefficient of every non-empty
 // subtuple S (itself included); the empty subtuple is counted in coef_ref.
+// With pi-pruning (partner != NULL) the subtuples are the unions of units
+// and the sign counts units.
 __global__ void k_mbe_coef(DevHash h, const int32_t* __restrict__ tuples, int order, int64_t ntup,
-                           int32_t* __restrict__ coef, int32_t* __restrict__ coef_ref,
-                           int32_t* __restrict__ err) {
+                           const int32_t* __restrict__ partner, int32_t* __restrict__ coef,
+                           int32_t* __restrict__ coef_ref, int32_t* __restrict__ err) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= ntup) return;
   int orb[MBE_MAX_ORDER];
+  unsigned pb[MBE_MAX_ORDER];
   for (int i = 0; i < order; i++) orb[i] = tuples[t * order + i];
+  partner_bits(orb, order, partner, pb);
   const unsigned full = (1u << order) - 1u;
+  const int nt = partner ? unit_count(full, pb, order) : order;
   for (unsigned m = 1; m <= full; m++) {
+    if (partner && !unit_closed(m, pb, order)) continue;
     unsigned long long k0 = 0, k1 = 0;
     for (int i = 0; i < order; i++)
       if ((m >> i) & 1u) {
@@ -235,9 +272,72 @@ __global__ void k_mbe_coef(DevHash h, const int32_t* __restrict__ tuples, int or
       atomicExch(err, MBE_ELOOKUP);
       continue;
     }
-    atomicAdd(&coef[slot], ((order - __popc(m)) & 1) ? -1 : 1);
+    const int ns = partner ? unit_count(m, pb, order) : __popc(m);
+    atomicAdd(&coef[slot], ((nt - ns) & 1) ? -1 : 1);
   }
-  atomicAdd(coef_ref, (order & 1) ? -1 : 1);
+  atomicAdd(coef_ref, (nt & 1) ? -1 : 1);
+}
+
+// pi-pruned generation: candidate (parent p of order kp, unit u) with the
+// unit (ua, ub) (ub = -1 for a single orbital) added; formed iff the unit's
+// lowest orbital exceeds the lowest orbital of every unit of the parent (each
+// tuple has one canonical parent), every one-unit-removed subtuple exists
+// (the empty one is the reference space) and, if any exists besides the
+// empty one, at least one of them is kept.  Writes the tuple sorted.
+__device__ bool candidate_ok_units(const DevHash& h, const int32_t* parents, int kp, int64_t p,
+                                   const int32_t* ua, const int32_t* ub, int u,
+                                   const int32_t* __restrict__ partner, int* orb) {
+  const int32_t* par = parents + p * kp;
+  const int a = ua[u], b = ub[u];
+  for (int i = 0; i < kp; i++) {
+    const int o = par[i], q = partner[o];
+    const int lo = q >= 0 && q < o ? q : o;        // lowest orbital of o's unit
+    if (lo >= a) return false;
+  }
+  const int k = kp + (b >= 0 ? 2 : 1);
+  int n = 0, ia = 0;
+  // merge the unit's orbitals into the sorted parent
+  for (int i = 0; i < kp; i++) {
+    while (ia < 2 && (ia == 0 ? a : b) >= 0 && (ia == 0 ? a : b) < par[i]) orb[n++] = ia++ == 0 ? a : b;
+    orb[n++] = par[i];
+  }
+  while (ia < 2 && (ia == 0 ? a : b) >= 0) orb[n++] = ia++ == 0 ? a : b;
+  if (n != k) return false;
+  unsigned pb[MBE_MAX_ORDER + 2];
+  partner_bits(orb, k, partner, pb);
+  bool any_keep = false, any = false;
+  for (int drop = 0; drop < k; drop++) {
+    // remove the unit of position drop (once per unit: from its first member)
+    if (pb[drop] && pb[drop] < (1u << drop)) continue;
+    const unsigned rm = (1u << drop) | pb[drop];
+    unsigned long long k0 = 0, k1 = 0;
+    int cnt = 0;
+    for (int i = 0; i < k; i++) {
+      if ((rm >> i) & 1u) continue;
+      const int x = orb[i];
+      if (x < 64) k0 |= 1ull << x; else k1 |= 1ull << (x - 64);
+      cnt++;
+    }
+    if (cnt == 0) continue;                        // the reference space
+    any = true;
+    const int64_t slot = hash_find(h, k0, k1);
+    if (slot < 0) return false;
+    if (h.keep[slot]) any_keep = true;
+  }
+  return any ? any_keep : true;
+}
+
+__global__ void k_gen_units(DevHash h, const int32_t* __restrict__ parents, int kp, int64_t np,
+                            const int32_t* __restrict__ ua, const int32_t* __restrict__ ub, int nu,
+                            const int32_t* __restrict__ partner, int k,
+                            int32_t* __restrict__ count, int32_t* __restrict__ out, int64_t cap) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= np * nu) return;
+  int orb[MBE_MAX_ORDER + 2];
+  if (!candidate_ok_units(h, parents, kp, c / nu, ua, ub, (int)(c % nu), partner, orb)) return;
+  const int pos = atomicAdd(count, 1);
+  if (pos < cap)
+    for (int i = 0; i < k; i++) out[(int64_t)pos * k + i] = orb[i];
 }
 
 DevHash dev_hash(mbe_ctx* ctx) {
@@ -287,8 +387,70 @@ void increments_kernel_launch(mbe_ctx* ctx, const int32_t* tuples_dev, int order
                               uint8_t* keep_dev, int32_t* err_dev) {
   if (ntup == 0) return;
   k_increments<<<(unsigned)((ntup + 127) / 128), 128, 0, ctx->stream>>>(
-      dev_hash(ctx), tuples_dev, order, ntup, eps_dev, eps_ref, thr, inc_dev, keep_dev, err_dev);
+      dev_hash(ctx), tuples_dev, order, ntup, eps_dev, eps_ref, thr,
+      ctx->pruned ? ctx->partner_dev.ptr : nullptr, inc_dev, keep_dev, err_dev);
   CU_LAUNCH_CHECK();
+}
+
+// pi-pruned tuples of order k: single units added to the order-(k-1) tuples
+// and pair units added to the order-(k-2) tuples (for k = 2 the empty tuple),
+// in lexicographic order
+std::vector<int32_t> next_tuples_pruned(mbe_ctx* ctx, int k) {
+  std::vector<int32_t> sa, sb, pa, pbv;
+  for (int o : ctx->exp) {
+    const int q = ctx->partner[o];
+    if (q < 0) {
+      sa.push_back(o);
+      sb.push_back(-1);
+    } else if (o < q) {
+      pa.push_back(o);
+      pbv.push_back(q);
+    }
+  }
+  auto level = [&](int order) -> std::vector<int32_t> {
+    for (const OrderRec& r : ctx->history)
+      if (r.order == order) return r.tuples;
+    return {};
+  };
+  std::vector<std::vector<int32_t>> found;
+  DevHash h = dev_hash(ctx);
+  for (int pass = 0; pass < 2; pass++) {
+    const int kp = k - (pass == 0 ? 1 : 2);
+    const std::vector<int32_t>& ua = pass == 0 ? sa : pa;
+    const std::vector<int32_t>& ub = pass == 0 ? sb : pbv;
+    if (kp < 0 || ua.empty()) continue;
+    std::vector<int32_t> par = kp == 0 ? std::vector<int32_t>{} : level(kp);
+    const int64_t np = kp == 0 ? 1 : (int64_t)par.size() / kp;
+    if (np == 0) continue;
+    const int nu = (int)ua.size();
+    DevBuf<int32_t> dpar(&ctx->pool, std::max<size_t>(1, par.size())), dua(&ctx->pool, nu),
+        dub(&ctx->pool, nu), cnt(&ctx->pool, 1);
+    if (!par.empty())
+      CU_CHECK(cudaMemcpyAsync(dpar.ptr, par.data(), sizeof(int32_t) * par.size(),
+                               cudaMemcpyHostToDevice, ctx->stream));
+    CU_CHECK(cudaMemcpyAsync(dua.ptr, ua.data(), sizeof(int32_t) * nu, cudaMemcpyHostToDevice,
+                             ctx->stream));
+    CU_CHECK(cudaMemcpyAsync(dub.ptr, ub.data(), sizeof(int32_t) * nu, cudaMemcpyHostToDevice,
+                             ctx->stream));
+    const int64_t cap = np * nu;
+    DevBuf<int32_t> out(&ctx->pool, (size_t)cap * k);
+    CU_CHECK(cudaMemsetAsync(cnt.ptr, 0, sizeof(int32_t), ctx->stream));
+    k_gen_units<<<(unsigned)((cap + 255) / 256), 256, 0, ctx->stream>>>(
+        h, dpar.ptr, kp, np, dua.ptr, dub.ptr, nu, ctx->partner_dev.ptr, k, cnt.ptr, out.ptr, cap);
+    CU_LAUNCH_CHECK();
+    int32_t n = 0;
+    CU_CHECK(cudaMemcpyAsync(&n, cnt.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    CU_CHECK(cudaStreamSynchronize(ctx->stream));
+    std::vector<int32_t> hv((size_t)n * k);
+    if (n)
+      CU_CHECK(cudaMemcpy(hv.data(), out.ptr, sizeof(int32_t) * hv.size(), cudaMemcpyDeviceToHost));
+    for (int32_t i = 0; i < n; i++) found.emplace_back(hv.begin() + (size_t)i * k, hv.begin() + (size_t)(i + 1) * k);
+  }
+  std::sort(found.begin(), found.end());
+  std::vector<int32_t> flat;
+  flat.reserve(found.size() * k);
+  for (const auto& t : found) flat.insert(flat.end(), t.begin(), t.end());
+  return flat;
 }
 
 double kahan_sum_device(mbe_ctx* ctx, const double* v, int64_t n) {
@@ -334,6 +496,7 @@ void mbe_coef_launch(mbe_ctx* ctx, const int32_t* tuples_dev, int order, int64_t
                      int32_t* coef_dev, int32_t* coef_ref_dev, int32_t* err_dev) {
   if (ntup == 0) return;
   k_mbe_coef<<<(unsigned)((ntup + 127) / 128), 128, 0, ctx->stream>>>(
-      dev_hash(ctx), tuples_dev, order, ntup, coef_dev, coef_ref_dev, err_dev);
+      dev_hash(ctx), tuples_dev, order, ntup, ctx->pruned ? ctx->partner_dev.ptr : nullptr,
+      coef_dev, coef_ref_dev, err_dev);
   CU_LAUNCH_CHECK();
 }

@@ -238,6 +238,11 @@ struct mbe_ctx {
   KeptCI ref_ci;
   // warm-start vectors of the previous and the current order
   GuessStore guess_prev, guess_cur;
+  // pi-pruning: partner[o] = the degenerate partner of expansion orbital o
+  // (-1 if none); tuples are unions of units (single orbitals and pairs)
+  bool pruned = false;
+  std::vector<int32_t> partner;
+  DevBuf<int32_t> partner_dev;
 
   ~mbe_ctx();
 };
@@ -371,6 +376,8 @@ double kahan_sum_device(mbe_ctx* ctx, const double* v, int64_t n);
 // hash slot) and coef_ref (the empty tuple)
 void mbe_coef_launch(mbe_ctx* ctx, const int32_t* tuples_dev, int order, int64_t ntup,
                      int32_t* coef_dev, int32_t* coef_ref_dev, int32_t* err_dev);
+// tuples of order k of a pi-pruned expansion (host rows, lexicographic)
+std::vector<int32_t> next_tuples_pruned(mbe_ctx* ctx, int k);
 int64_t next_tuples_device(mbe_ctx* ctx, const int32_t* parents_dev, int order_prev,
                            int64_t nparents, const int32_t* exp_dev, int nexp,
                            DevBuf<int32_t>& out);

@@ -93,27 +93,37 @@ def torch_allreduce_sum(group=None):
 
 
 def run_expansion(ctx, ref, exp, max_order, thr=0.0, rank=0, world=1, allgather=None,
-                  solve=None, callback=None, api=None, nocc=None):
+                  solve=None, callback=None, api=None, nocc=None, pairs=None):
     """Run orders 1..max_order; returns dict(eps_ref, orders, total, ntup).
 
     ``api`` is the module of C-ABI wrappers (default: the binding);
     ``solve(ctx, tuples, k) -> eps`` defaults to its mbe_solve_tuples.  Tests
     pass a host stand-in for both to exercise the sharding logic without a
     GPU.  With ``nocc`` (occupied orbitals of the reference determinant) the
-    shares are weighted by the tuples' determinant counts."""
+    shares are weighted by the tuples' determinant counts.  ``pairs`` of
+    degenerate expansion orbitals switch on pi-pruning (Sec. 3)."""
     B_ = api or B
     if solve is None:
         def solve(c, t, k):
             return B_.mbe_solve_tuples(c, t, k)[0]
     e_ref = B_.mbe_set_reference(ctx, ref, exp)
+    if pairs:
+        B_.mbe_set_pruning_pairs(ctx, pairs)
     orders = []
     total = e_ref
     ntot = 0
+    empty_run = 0
     for k in range(1, max_order + 1):
-        tuples = B_.mbe_next_tuples(ctx, k)
+        tuples = B_.mbe_next_tuples(ctx, k).reshape(-1, k)
         n = len(tuples)
         if n == 0:
-            break
+            # with pruning an empty order can precede a non-empty one (a pair
+            # adds two orbitals); two empty orders end the expansion
+            empty_run += 1
+            if empty_run >= (2 if pairs else 1):
+                break
+        else:
+            empty_run = 0
         wts = tuple_weights(tuples, ref, nocc) if (nocc is not None and world > 1) else None
         mine = shard_indices(n, rank, world, wts)
         eps_local = solve(ctx, tuples[mine], k) if len(mine) else np.zeros(0)

@@ -312,3 +312,65 @@ def test_sigma_rows_equals_dense_rows():
     assert sp.sigma_rows(c, np.array([], dtype=np.int64)).size == 0
     with pytest.raises(ValueError):
         sp.sigma_rows(c, [sp.ndet])
+
+
+def _pruned_counts(nsingle, npairs, max_order):
+    """Unscreened tuple counts of a pi-pruned expansion (tuple enumeration of
+    the oracle, no energies needed)."""
+    exp = list(range(nsingle + 2 * npairs))
+    pairs = [(nsingle + 2 * i, nsingle + 2 * i + 1) for i in range(npairs)]
+    formed, counts = {}, []
+    for k in range(1, max_order + 1):
+        t = om.next_order_tuples_pruned(exp, pairs, formed, 0.0, k)
+        formed.update({x: 1.0 for x in t})
+        counts.append(len(t))
+    return counts
+
+
+def test_pi_pruned_counts_match_paper():
+    """Table 2 (pi-pruned columns): 6, 21, 56, 120, 216 tuples at orders 1-5
+    for 6 single orbitals and 6 degenerate pairs; the same counts follow from
+    the closed form sum_j C(6, k - 2j) C(6, j)."""
+    gold = {}
+    with open(os.path.join(GOLDEN, "paper_pi_pruned_counts.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, c = line.split()
+                gold[int(k)] = int(c)
+    counts = _pruned_counts(6, 6, max(gold))
+    assert {k: counts[k - 1] for k in gold} == gold
+    closed = [sum(math.comb(6, k - 2 * j) * math.comb(6, j) for j in range(k // 2 + 1)
+                  if k - 2 * j >= 0) for k in range(1, max(gold) + 1)]
+    assert counts == closed
+
+
+def test_pi_pruned_allorder_equals_fci_and_mobius():
+    """Unscreened and to all orders the pruned expansion (units: single
+    orbitals and degenerate pairs) sums to the FCI energy of the whole space;
+    every increment equals its Moebius form over the unit lattice; without
+    pairs the pruned bookkeeping reproduces the standard expansion."""
+    n, nocc = 9, 3
+    h, eri, _ = ms.gen_integrals(n, nocc, 5)
+    ref, exp, pairs = [1, 2], [0, 3, 4, 5, 6, 7, 8], [(3, 4), (6, 8)]
+    res = om.run_mbe(h, eri, nocc, ref, exp, 7, 0.0, pairs=pairs)
+    assert abs(res["total"] - oc.casci(h, eri, nocc, list(range(n)))) < 1e-10
+    # no tuple splits a pair; order 2 holds the two pairs alone
+    for o in res["orders"]:
+        for t in o["tuples"]:
+            for a, b in pairs:
+                assert (a in t) == (b in t)
+    assert (3, 4) in res["orders"][1]["tuples"] and (6, 8) in res["orders"][1]["tuples"]
+    units = om.expansion_units(exp, pairs)
+    for t, d in res["inc"].items():
+        assert abs(d - om.increment_mobius_units(t, res["eps"], res["eps_ref"], units)) < 1e-10
+    # E = sum_S c_S eps_S with coefficients that count units
+    coef = om.mbe_coefficients(list(res["inc"].keys()), units)
+    e = coef[()] * res["eps_ref"] + sum(c * res["eps"][s] for s, c in coef.items() if s)
+    assert abs(e - res["total"]) < 1e-10
+    # without pairs every unit is one orbital: the unit enumeration gives the
+    # standard tuples of the screened expansion order by order
+    std = om.run_mbe(h, eri, nocc, ref, exp, 4, 1e-3)
+    formed = {}
+    for k, o in enumerate(std["orders"], start=1):
+        assert om.next_order_tuples_pruned(exp, [], formed, 1e-3, k) == o["tuples"]
+        formed.update(dict(zip(o["tuples"], o["inc"])))
