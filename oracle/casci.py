@@ -13,11 +13,20 @@ determinants live in the FULL orbital space (core bits set, deleted bits
 clear) and the matrix elements are the Slater-Condon rules of ``sc_fci.c``,
 so the energy is the total electronic energy including the inactive core.
 
-Target state: the lowest singlet (S = 0).  It lies in the subspace
+Target state, closed-shell reference (``nocc`` an int: orbitals below it
+doubly occupied): the lowest singlet (S = 0).  It lies in the subspace
 C[Ia, Ib] = C[Ib, Ia] (alpha <-> beta exchange symmetric, Ms = 0) of the
 determinant convention a+_{alpha string} a+_{beta string}|0>, which holds
 the even-S states; the synthetic integrals often put a quintet below the
 lowest singlet there, so the singlet is selected explicitly.
+
+High-spin open-shell reference (Fig. 2 case (b); ``nocc`` a pair
+(n_alpha, n_beta), n_alpha > n_beta: orbitals below n_beta doubly occupied,
+those from n_beta to n_alpha - 1 singly occupied by alpha electrons): the
+determinant space has Ms = (n_alpha - n_beta) / 2 and the target is the
+lowest state with S = Ms.  The singly occupied orbitals must be active (the
+inactive core stays closed-shell); the space is the full alpha-string x
+beta-string product, with no alpha <-> beta symmetry.
 
 Solvers: dense ``numpy.linalg.eigh`` of the projected symmetric-subspace
 matrix for up to 5000 determinants, taking the lowest eigenvector whose
@@ -71,6 +80,16 @@ def _up(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
 
 
+def occ_pair(nocc):
+    """(n_alpha, n_beta) occupied orbitals of the reference determinant."""
+    if isinstance(nocc, (tuple, list)):
+        na, nb = int(nocc[0]), int(nocc[1])
+        if na < nb or nb < 0:
+            raise ValueError("high-spin reference needs n_alpha >= n_beta >= 0")
+        return na, nb
+    return int(nocc), int(nocc)
+
+
 def tuple_strings(nocc: int, act):
     """Sorted full-space strings of one spin for the CASCI of ``act``.
 
@@ -96,27 +115,40 @@ def tuple_strings(nocc: int, act):
 
 
 class Space:
-    """Determinant space (alpha strings x beta strings) with the integrals."""
+    """Determinant space (alpha strings x beta strings) with the integrals.
+
+    ``nocc``: an int (closed shell) or (n_alpha, n_beta) (high spin)."""
 
     def __init__(self, h, eri, nocc, act):
         self.h = np.ascontiguousarray(h, dtype=np.float64)
         self.eri = np.ascontiguousarray(eri, dtype=np.float64)
         self.norb = self.h.shape[0]
-        self.strs, self.nsig = tuple_strings(nocc, act)
-        self.nstr = self.strs.shape[0]
-        self.ndet = self.nstr * self.nstr
+        na, nb = occ_pair(nocc)
+        act_set = set(int(a) for a in act)
+        if any(o not in act_set for o in range(nb, na)):
+            raise ValueError("singly occupied orbitals must be active")
+        self.astrs, self.nsig = tuple_strings(na, act)
+        self.bstrs, self.nsigb = tuple_strings(nb, act)
+        self.strs = self.astrs
+        self.nstr = self.astrs.shape[0]
+        self.nstrb = self.bstrs.shape[0]
+        self.ndet = self.nstr * self.nstrb
+        # Ms of every determinant of the space
+        self.ms = 0.5 * (self.nsig - self.nsigb)
+
+    def _args(self):
+        return (self.nstr, _up(self.astrs), self.nstrb, _up(self.bstrs))
 
     def hdiag(self):
         out = np.empty(self.ndet)
-        lib().oracle_hdiag(self.norb, _dp(self.h), _dp(self.eri), self.nstr, _up(self.strs),
-                           self.nstr, _up(self.strs), _dp(out))
+        lib().oracle_hdiag(self.norb, _dp(self.h), _dp(self.eri), *self._args(), _dp(out))
         return out
 
     def sigma(self, c):
         c = np.ascontiguousarray(c, dtype=np.float64).ravel()
         out = np.empty(self.ndet)
-        lib().oracle_sigma(self.norb, _dp(self.h), _dp(self.eri), self.nstr, _up(self.strs),
-                           self.nstr, _up(self.strs), _dp(c), _dp(out))
+        lib().oracle_sigma(self.norb, _dp(self.h), _dp(self.eri), *self._args(), _dp(c),
+                           _dp(out))
         return out
 
     def sigma_rows(self, c, rows):
@@ -126,38 +158,34 @@ class Space:
         if rows.size and (rows.min() < 0 or rows.max() >= self.ndet):
             raise ValueError("row index out of range")
         out = np.empty(rows.size)
-        lib().oracle_sigma_rows(self.norb, _dp(self.h), _dp(self.eri), self.nstr,
-                                _up(self.strs), self.nstr, _up(self.strs), _dp(c), rows.size,
-                                rows.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), _dp(out))
+        lib().oracle_sigma_rows(self.norb, _dp(self.h), _dp(self.eri), *self._args(), _dp(c),
+                                rows.size, rows.ctypes.data_as(ctypes.POINTER(ctypes.c_long)),
+                                _dp(out))
         return out
 
     def hdense(self):
         H = np.empty((self.ndet, self.ndet))
-        lib().oracle_hdense(self.norb, _dp(self.h), _dp(self.eri), self.nstr, _up(self.strs),
-                            self.nstr, _up(self.strs), _dp(H))
+        lib().oracle_hdense(self.norb, _dp(self.h), _dp(self.eri), *self._args(), _dp(H))
         return H
 
     def s2(self, c):
-        """S^2 c (Ms = 0)."""
+        """S^2 c = S- S+ c + Ms (Ms + 1) c."""
         c = np.ascontiguousarray(c, dtype=np.float64).ravel()
         out = np.empty(self.ndet)
-        lib().oracle_s2(self.norb, self.nstr, _up(self.strs), self.nstr, _up(self.strs),
-                        _dp(c), _dp(out), None)
-        return out
+        lib().oracle_s2(self.norb, *self._args(), _dp(c), _dp(out), None)
+        return out + self.ms * (self.ms + 1.0) * c
 
     def s2diag(self):
         out = np.empty(self.ndet)
-        lib().oracle_s2(self.norb, self.nstr, _up(self.strs), self.nstr, _up(self.strs),
-                        None, None, _dp(out))
-        return out
+        lib().oracle_s2(self.norb, *self._args(), None, None, _dp(out))
+        return out + self.ms * (self.ms + 1.0)
 
     def rdm12(self, c):
         c = np.ascontiguousarray(c, dtype=np.float64).ravel()
         n = self.norb
         g1 = np.empty((n, n))
         g2 = np.empty((n, n, n, n))
-        lib().oracle_rdm12(n, self.nstr, _up(self.strs), self.nstr, _up(self.strs),
-                           _dp(c), _dp(g1), _dp(g2))
+        lib().oracle_rdm12(n, *self._args(), _dp(c), _dp(g1), _dp(g2))
         return g1, g2
 
     def sym_basis(self):
@@ -183,9 +211,12 @@ def _symmetrize(v, n):
 
 def davidson(space: Space, tol_r=1e-8, tol_e=1e-13, max_iter=300, max_space=30,
              guess=None, spin_shift=SPIN_SHIFT):
-    """Lowest root of H + spin_shift * S^2 in the symmetric subspace;
-    returns (E, c, iters) with E = c.Hc of the normalised root."""
+    """Lowest root of H + spin_shift * S^2, in the symmetric subspace for a
+    closed-shell space (in the whole space for a high-spin one); returns
+    (E, c, iters) with E = c.Hc of the normalised root."""
     n = space.nstr
+    sym = space.ms == 0
+    proj = (lambda v: _symmetrize(v, n)) if sym else (lambda v: v)
     hd = space.hdiag()
     if spin_shift:
         hd = hd + spin_shift * space.s2diag()
@@ -198,13 +229,16 @@ def davidson(space: Space, tol_r=1e-8, tol_e=1e-13, max_iter=300, max_space=30,
 
     if guess is None:
         i0 = int(np.argmin(hd))
-        a, b = divmod(i0, n)
         x0 = np.zeros(space.ndet)
-        x0[a * n + b] += 1.0
-        x0[b * n + a] += 1.0
+        if sym:
+            a, b = divmod(i0, n)
+            x0[a * n + b] += 1.0
+            x0[b * n + a] += 1.0
+        else:
+            x0[i0] = 1.0
     else:
         x0 = np.array(guess, dtype=np.float64).ravel()
-    x0 = _symmetrize(x0, n)
+    x0 = proj(x0)
     x0 /= np.linalg.norm(x0)
     V = [x0]
     S = [op(x0)]
@@ -230,7 +264,7 @@ def davidson(space: Space, tol_r=1e-8, tol_e=1e-13, max_iter=300, max_space=30,
             S = [ax / nx]
         den = theta - hd
         den = np.where(np.abs(den) < 1e-8, np.copysign(1e-8, den), den)
-        t = _symmetrize(r / den, n)
+        t = proj(r / den)
         for _ in range(2):
             for v in V:
                 t -= (v @ t) * v
@@ -253,15 +287,17 @@ def casci(h, eri, nocc, act, want_vector=False, dense_max=DENSE_MAX):
     if sp.ndet <= dense_max:
         H = sp.hdense()
         H = 0.5 * (H + H.T)
-        P = sp.sym_basis()
+        # S = Ms: <S^2> = Ms(Ms+1); the next spin has Ms(Ms+1) + 2Ms + 2
+        target = sp.ms * (sp.ms + 1.0)
+        P = sp.sym_basis() if sp.ms == 0 else np.eye(sp.ndet)
         w, U = np.linalg.eigh(P.T @ H @ P)
         for k in range(len(w)):
             c = P @ U[:, k]
-            if c @ sp.s2(c) < 0.5:
+            if c @ sp.s2(c) < target + 0.5:
                 e = float(w[k])
                 break
         else:
-            raise RuntimeError("no singlet in the symmetric subspace")
+            raise RuntimeError("no state with S = Ms in the space")
     else:
         e, c, _ = davidson(sp)
     if want_vector:

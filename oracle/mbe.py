@@ -175,7 +175,8 @@ def increment_mobius_units(t, eps: dict, eps_ref: float, units) -> float:
 def run_mbe(h, eri, nocc, ref, exp, max_order, thr=0.0, solver=None, keep_vectors=False,
             pairs=None):
     """Run the expansion (pi-pruned over ``pairs`` of degenerate expansion
-    orbitals if given).  Returns a dict with the reference energy, per
+    orbitals if given); ``nocc`` is an int (closed-shell reference) or
+    (n_alpha, n_beta) for a high-spin one (Fig. 2 case (b)).  Returns a dict with the reference energy, per
     order lists (tuples, eps, inc, keep, E_order) and the total (Kahan)."""
     if solver is None:
         def solver(act):

@@ -254,11 +254,13 @@ def test_mbe_coefficients_allorder():
         assert c == (1 if t == (0, 1, 2, 3) else 0)
 
 
-def test_gradient_central_fd():
+@pytest.mark.parametrize("nocc", [2, (3, 1)])
+def test_gradient_central_fd(nocc):
     """Oracle Hellmann-Feynman gradient vs central finite differences of the
-    whole MBE energy (step 1e-5) on random unique integrals."""
-    n, nocc = 6, 2
-    h, eri, _ = ms.gen_integrals(n, nocc, 17)
+    whole MBE energy (step 1e-5) on random unique integrals; closed-shell and
+    high-spin (triplet) references."""
+    n = 6
+    h, eri, _ = ms.gen_integrals(n, 2, 17)
     ref, exp = [1, 2], [0, 3, 4, 5]
     tuples = [t for k in range(1, 3) for t in itertools.combinations(exp, k)]
     dh, dg, _ = om.mbe_gradient(h, eri, nocc, ref, tuples)
@@ -374,3 +376,81 @@ def test_pi_pruned_allorder_equals_fci_and_mobius():
     for k, o in enumerate(std["orders"], start=1):
         assert om.next_order_tuples_pruned(exp, [], formed, 1e-3, k) == o["tuples"]
         formed.update(dict(zip(o["tuples"], o["inc"])))
+
+
+# ---------------------------------------------------------------- open shell
+# High-spin references (Fig. 2 case (b)): nocc = (n_alpha, n_beta).
+
+@pytest.mark.parametrize("seed,norb,nocc,act", [
+    (3, 6, (3, 1), list(range(6))),
+    (7, 7, (4, 2), [1, 2, 3, 4, 5, 6]),      # orbital 0: inactive core
+    (11, 7, (4, 1), list(range(7))),          # quartet (Ms = 3/2)
+])
+def test_open_shell_energy_is_ms0_spin_eigenvalue(seed, norb, nocc, act):
+    """The lowest S = Ms state of the Ms = (na - nb)/2 space is an eigenvalue
+    of the same Hamiltonian in the Ms = 0 (or 1/2) space of the same electron
+    count: dense diagonalisation of the whole lower-Ms space (no symmetry
+    restriction), the lowest eigenvalue whose <S^2> is S(S+1)."""
+    na, nb = nocc
+    h, eri, _ = ms.gen_integrals(norb, nb, seed)
+    e_hs = oc.casci(h, eri, nocc, act)
+    ntot = na + nb
+    lo = (ntot // 2 + ntot % 2, ntot // 2)
+    sp = oc.Space(h, eri, lo, act)
+    H = sp.hdense()
+    w, U = np.linalg.eigh(0.5 * (H + H.T))
+    S = 0.5 * (na - nb)
+    for k in range(len(w)):
+        c = U[:, k]
+        if abs(c @ sp.s2(c) - S * (S + 1)) < 1e-6:
+            assert abs(w[k] - e_hs) < 1e-10
+            break
+    else:
+        raise AssertionError("no S = Ms state in the lower-Ms space")
+
+
+def test_open_shell_single_determinant_closed_forms():
+    """Spaces of one determinant: the energy is the textbook sum over the
+    occupied spin-orbitals, h_ii once per electron, Coulomb for every pair,
+    exchange only between equal spins."""
+    n = 5
+    h, eri, _ = ms.gen_integrals(n, 1, 17)
+    G = ms.unpack_eri(eri, n)
+    J = lambda p, q: G[p, p, q, q]
+    K = lambda p, q: G[p, q, q, p]
+    # alpha {0, 1, 2}, beta {0}: core orbital 0, act {1, 2} singly occupied
+    e = oc.casci(h, eri, (3, 1), [1, 2])
+    ref = (2 * h[0, 0] + h[1, 1] + h[2, 2] + J(0, 0) + 2 * J(0, 1) - K(0, 1)
+           + 2 * J(0, 2) - K(0, 2) + J(1, 2) - K(1, 2))
+    assert abs(e - ref) < 1e-12
+    # doublet: alpha {0, 1}, beta {0}
+    e = oc.casci(h, eri, (2, 1), [1])
+    assert abs(e - (2 * h[0, 0] + h[1, 1] + J(0, 0) + 2 * J(0, 1) - K(0, 1))) < 1e-12
+    # two alpha electrons in orbitals 0 and 1, no beta electron
+    e = oc.casci(h, eri, (2, 0), [0, 1])
+    assert abs(e - (h[0, 0] + h[1, 1] + J(0, 1) - K(0, 1))) < 1e-12
+
+
+def test_open_shell_rdm_energy_and_traces():
+    """tr gamma = N, sum Gamma_ppqq = N(N-1), E = h.gamma + 1/2 (pq|rs).Gamma
+    for a high-spin CASCI with an inactive core."""
+    n, nocc = 7, (4, 2)
+    h, eri, _ = ms.gen_integrals(n, 2, 23)
+    e, c, sp = oc.casci(h, eri, nocc, [1, 2, 3, 4, 6], want_vector=True)
+    g1, g2 = sp.rdm12(c)
+    N = 6
+    assert abs(np.trace(g1) - N) < 1e-12
+    assert abs(np.einsum("ppqq", g2) - N * (N - 1)) < 1e-11
+    G = ms.unpack_eri(eri, n)
+    assert abs(np.einsum("pq,pq", h, g1) + 0.5 * np.einsum("pqrs,pqrs", G, g2) - e) < 1e-11
+    assert abs(c @ sp.s2(c) - 2.0) < 1e-8
+
+
+def test_open_shell_allorder_mbe_is_fci():
+    """Unscreened to all orders the expansion around a high-spin CAS
+    reference telescopes to the CASCI of the whole space (Eq. 3)."""
+    n, nocc = 7, (3, 1)
+    h, eri, _ = ms.gen_integrals(n, 1, 29)
+    ref, exp = [1, 2], [0, 3, 4, 5, 6]
+    res = om.run_mbe(h, eri, nocc, ref, exp, len(exp))
+    assert abs(res["total"] - oc.casci(h, eri, nocc, list(range(n)))) < 1e-10
