@@ -184,6 +184,75 @@ def run_reference(args):
     return 0
 
 
+def run_fd_check(args):
+    """Central differences of the GPU energy against the analytic gradient
+    (mbe_energy_backward) on N seeded unique integrals of the differentiation
+    workload (8e/20o, CAS(4e,4o) reference, unscreened to order 4, FP64):
+    each entry h_pq (with h_qp) or (pq|rs) (with all its images) is moved by
+    +-step and the difference quotient compared with the gradient entry.
+    Prints one JSON line with the error distribution."""
+    from paper_1905_02786_gb300 import build, _binding as B
+    build.build()
+    B.load_library()
+    name = "grad_8e20o"
+    w = ms.workload(name)
+    h, eri, _ = ms.workload_integrals(name)
+    n, P = w["norb"], ms.npair(w["norb"])
+    tight = dict(conv_tol_r=1e-11, conv_tol_e=1e-14)
+    m = B.MBE(0, keep_ci=1, **tight)
+    m.load(h, eri, w["nel"])
+    m.run(w["ref"], w["exp"], w["max_order"], 0.0)
+    dh, dg = m.backward()
+    m.close()
+    e0 = B.MBE(0, **tight)
+
+    def energy(h_, e_):
+        e0.load(h_, e_, w["nel"])
+        return e0.run(w["ref"], w["exp"], w["max_order"], 0.0)["total"]
+
+    rng = np.random.default_rng(args.fd_seed)
+    step = args.fd_step
+    rows = []
+    t0 = time.perf_counter()
+    for i in range(args.fd_check):
+        if i % 2 == 0:
+            p, q = sorted(int(x) for x in rng.integers(0, n, 2))
+            hp, hm = h.copy(), h.copy()
+            for M, s in ((hp, step), (hm, -step)):
+                M[p, q] += s
+                if p != q:
+                    M[q, p] += s
+            fd = (energy(hp, eri) - energy(hm, eri)) / (2 * step)
+            an = dh[p, q] * (1 if p == q else 2)
+            rows.append(("h", p, q, fd, an))
+        else:
+            a, b = sorted(int(x) for x in rng.integers(0, P, 2))
+            ep, em = eri.copy(), eri.copy()
+            for M, s in ((ep, step), (em, -step)):
+                M[a, b] += s
+                if a != b:
+                    M[b, a] += s
+            fd = (energy(h, ep) - energy(h, em)) / (2 * step)
+            an = dg[a, b] * (1 if a == b else 2)
+            rows.append(("eri", a, b, fd, an))
+    e0.close()
+    err = np.array([abs(r[3] - r[4]) for r in rows])
+    mag = np.array([abs(r[4]) for r in rows])
+    big = mag >= 0.1
+    rel_big = err[big] / mag[big] if big.any() else np.zeros(0)
+    out = {"fd_check": len(rows), "workload": name, "step": step, "seed": args.fd_seed,
+           "seconds": time.perf_counter() - t0,
+           "max_abs_error": float(err.max()), "median_abs_error": float(np.median(err)),
+           "entries_with_abs_grad_ge_0.1": int(big.sum()),
+           "max_rel_error_abs_grad_ge_0.1": float(rel_big.max()) if big.any() else None,
+           "within_1e-6_rel_plus_2e-7": int(np.sum(err <= 1e-6 * mag + 2e-7)),
+           "within_1e-6_rel": int(np.sum(err <= 1e-6 * mag)),
+           "max_abs_grad": float(mag.max()), "min_abs_grad": float(mag.min()),
+           "trace_dh_minus_nel": float(np.trace(dh) - w["nel"])}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def transfer_bytes(res, h, eri):
     """Bytes that cross the C ABI per expansion: tuples out of next_tuples,
     tuples into solve, energies/status/increments/keep back."""
@@ -246,6 +315,14 @@ def main():
     ap.add_argument("--max-batch", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--fd-check", type=int, default=0,
+                    help="finite-difference check of the energy gradient on this many "
+                         "seeded unique integrals of the differentiation workload")
+    ap.add_argument("--fd-step", type=float, default=1e-5)
+    ap.add_argument("--fd-seed", type=int, default=3)
+    ap.add_argument("--backward", action="store_true",
+                    help="keep the CI vectors and run the energy backward (dE/dh, "
+                         "dE/d(pq|rs)) inside every step")
     ap.add_argument("--profile-batch", type=int, default=0,
                     help="profiling case instead of the bench: solve this many seeded "
                          "order-6 tuples of the workload as one batch inside the NVTX "
@@ -258,6 +335,8 @@ def main():
         return run_reference(args)
     if args.profile_batch:
         return run_profile_batch(args)
+    if args.fd_check:
+        return run_fd_check(args)
 
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -275,7 +354,9 @@ def main():
     h, eri, _ = ms.workload_integrals(args.workload)
     max_order = args.max_order or w["max_order"]
     prec = B.MBE_MIXED_BF16X3 if args.precision == "mixed" else B.MBE_FP64
-    m = B.MBE(local, precision=prec, max_batch=args.max_batch, timing=1)
+    m = B.MBE(local, precision=prec, max_batch=args.max_batch, timing=1,
+              keep_ci=1 if args.backward else 0,
+              backward_share=(2 if rank == 0 else 1) if world > 1 else 0)
     stream = torch.cuda.Stream()
     B.mbe_set_stream(m.ctx, stream.cuda_stream)
     m.load(h, eri, w["nel"])
@@ -283,6 +364,7 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     order_s = []
+    bwd_s = []
 
     def step():
         # host-side seconds per order (the solve returns its energies to the
@@ -296,8 +378,14 @@ def main():
                             "s": round(t - t_last[0], 4)})
             t_last[0] = t
 
-        return driver.run_expansion(m.ctx, w["ref"], w["exp"], max_order, w["thr"], rank, world,
-                                    allgather, callback=mark, nocc=w["nocc"])
+        res = driver.run_expansion(m.ctx, w["ref"], w["exp"], max_order, w["thr"], rank, world,
+                                   allgather, callback=mark, nocc=w["nocc"])
+        if args.backward:
+            t0 = time.perf_counter()
+            driver.sharded_backward(m.ctx, w["norb"], rank, world,
+                                    driver.torch_allreduce_sum() if world > 1 else None)
+            bwd_s.append(time.perf_counter() - t0)
+        return res
 
     def barrier():
         if world > 1:
@@ -481,6 +569,7 @@ def main():
                     * st["sigma_vectors"] / max(st["casci"], 1)},
                 "davidson_iters_mean": st["iters_total"] / max(st["casci"], 1),
                 "seconds_per_order": list(order_s),
+                "backward_s_per_step": (sum(bwd_s[-args.steps:]) / args.steps) if bwd_s else None,
                 "noconv": st["noconv"],
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "measured_fp_peaks": fp_peaks,

@@ -85,7 +85,10 @@ typedef struct mbe_options {
   double conv_tol_r;    /* residual-norm tolerance of the Davidson iteration */
   double conv_tol_e;    /* energy-change tolerance                           */
   double spin_shift;    /* lambda of H + lambda S^2 (lifts S >= 2 states)    */
-  int keep_ci;          /* keep converged CI vectors for the energy backward */
+  int keep_ci;          /* keep, on the device, the packed active-space RDMs
+                           of every converged CASCI for the energy backward
+                           (formed from the vector right after its batch
+                           converges; the vector itself is not kept)       */
   int deterministic;    /* 1: fixed-order reductions only (no float atomics) */
   int64_t mem_cap_bytes;/* cap on device memory the context may allocate; 0 =
                            no cap (exceeding it returns MBE_ENOMEM)          */
@@ -94,8 +97,8 @@ typedef struct mbe_options {
   int verbose;          /* 1: print per-iteration Davidson residual summaries
                            to stderr                                         */
   int backward_share;   /* what mbe_energy_backward sums: 0 the whole
-                           expansion (every CI vector must be held here);
-                           1 only the tuples whose CI vectors this context
+                           expansion (every RDM set must be held here);
+                           1 only the tuples whose RDMs this context
                            holds (tuples sharded over contexts); 2 as 1 plus
                            the reference-space term (exactly one context of
                            a sharded run)                                    */
@@ -175,17 +178,33 @@ const char* mbe_last_error(const mbe_ctx* ctx);
 
 /* Load the molecular integrals (input of every CASCI of Sec. 2).
  *  norb   number of spatial orbitals (1..128)
- *  nelec  number of (correlated) electrons, even (closed-shell reference)
+ *  nelec  number of (correlated) electrons; the reference determinant is
+ *         the closed shell (even nelec) or the high-spin doublet (odd),
+ *         see mbe_set_spin
  *  h      norb*norb, eri npair*npair (see conventions); NaN/Inf -> EINVAL.
- * Resets the reference space, the increment hash and kept CI vectors. */
+ * Resets the reference space, the increment hash and kept RDMs. */
 int mbe_load_integrals(mbe_ctx* ctx, int norb, int nelec, const double* h,
                        const double* eri);
+
+/* Spin of the reference determinant (Fig. 2: case (a) closed shell, case
+ * (b) high-spin open shell).  two_sz = n_alpha - n_beta >= 0 with the
+ * parity of nelec: orbitals 0 .. n_beta - 1 are doubly occupied, n_beta ..
+ * n_alpha - 1 singly occupied (alpha).  Every CASCI is then solved in the
+ * determinant space of that Ms = two_sz / 2 for its lowest S = Ms state;
+ * the singly occupied orbitals must belong to the reference space (checked
+ * by mbe_set_reference, MBE_EINVAL), so the inactive core stays closed-shell.
+ * Open-shell spaces run on the FP64 path (FP64-grade emulated contraction
+ * in the mixed and emulated modes; the split-BF16x3 sigma and the
+ * warm starts need alpha<->beta symmetric vectors).  MBE_EINVAL for a bad
+ * two_sz, MBE_ESTATE before mbe_load_integrals.  Resets the reference. */
+int mbe_set_spin(mbe_ctx* ctx, int two_sz);
 
 /* Set the reference space Pi (Sec. 2, Eq. 3) and the expansion space.
  *  ref_orbs[nref]  orbitals of Pi (distinct, any order)
  *  exp_orbs[nexp]  expansion orbitals (distinct, disjoint from Pi)
  * Solves the order-0 CASCI of Pi; its energy is written to *e_ref (may be
- * NULL).  Resets the increment hash. */
+ * NULL).  Resets the increment hash.  With a high-spin reference
+ * (mbe_set_spin) Pi must hold every singly occupied orbital. */
 int mbe_set_reference(mbe_ctx* ctx, const int* ref_orbs, int nref,
                       const int* exp_orbs, int nexp, double* e_ref);
 
@@ -244,7 +263,7 @@ int mbe_set_pruning_pairs(mbe_ctx* ctx, const int32_t* pairs, int npairs);
  * dE/d(pq|rs) = 1/2 sum_T c_T Gamma^T_pqrs, with full-space spin-summed RDMs
  * (inactive core included) and c_T = sum_{U in set, U >= T} (-1)^{|U|-|T|}.
  * Needs keep_ci = 1 when the reference and the tuples were solved.  With
- * opt.backward_share = 0 a tuple with a non-zero c_T whose CI vector is not
+ * opt.backward_share = 0 a tuple with a non-zero c_T whose RDMs are not
  * held returns MBE_ESTATE; with 1 or 2 such tuples are skipped (they were
  * solved by another context) so that the outputs of all contexts sum to the
  * gradient.
@@ -259,8 +278,8 @@ int mbe_energy_backward(mbe_ctx* ctx, double scale, double* dh, double* deri);
  * would, without solving.  Used when the tuples of one order are solved on
  * several GPUs: each process solves its share, the energies are gathered
  * and every process continues with mbe_increments on the full order.
- * Kept CI vectors (keep_ci) of tuples this context solved for this order
- * are retained. */
+ * Kept RDMs (keep_ci) of tuples this context solved for this order are
+ * retained. */
 int mbe_set_order_energies(mbe_ctx* ctx, int order, const int32_t* tuples,
                            int64_t ntup, const double* eps);
 
@@ -271,7 +290,10 @@ int mbe_reset_stats(mbe_ctx* ctx);
 
 /* Sigma vector of one CASCI for testing: sigma = (H_active + spin_shift*S^2)
  * c in the determinant basis of strings (Ia, Ib), in the context precision.
- *  act[nact]  active orbitals; c, sigma  nstr*nstr (host)
+ *  act[nact]  active orbitals; c, sigma  nstr_alpha*nstr_beta (host),
+ *             index Ia*nstr_beta + Ib (nstr_alpha = nstr_beta for a closed
+ *             shell; a high-spin reference, mbe_set_spin, needs its singly
+ *             occupied orbitals in act)
  * H_active excludes the inactive-core energy (returned in *e_core). */
 int mbe_sigma(mbe_ctx* ctx, const int* act, int nact, const double* c,
               double* sigma, double* e_core);
@@ -283,7 +305,8 @@ int mbe_sigma(mbe_ctx* ctx, const int* act, int nact, const double* c,
  * it serves callers that may not allocate: cudaMalloc / cudaFree can
  * synchronise the whole device, and a caller under a fixed device-memory
  * budget cannot let the context's pool grow).  Always the FP64 sigma
- * (H_active + spin_shift*S^2) c, whatever opt.precision says.
+ * (H_active + spin_shift*S^2) c, whatever opt.precision says; closed-shell
+ * references only (MBE_EINVAL after mbe_set_spin with two_sz > 0).
  *  act[nact]   active orbitals (host)
  *  c_dev       nstr*nstr doubles, DEVICE memory of the context's device,
  *              caller-owned, read only

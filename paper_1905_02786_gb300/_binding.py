@@ -25,7 +25,8 @@ EXPORTED = ["mbe_default_options", "mbe_create", "mbe_destroy", "mbe_last_error"
             "mbe_load_integrals", "mbe_set_reference", "mbe_solve_tuples",
             "mbe_increments", "mbe_next_tuples", "mbe_energy_backward", "mbe_sigma",
             "mbe_get_stats", "mbe_reset_stats", "mbe_set_order_energies", "mbe_set_stream",
-            "mbe_sigma_noalloc", "mbe_measure_peaks", "mbe_set_pruning_pairs"]
+            "mbe_sigma_noalloc", "mbe_measure_peaks", "mbe_set_pruning_pairs",
+            "mbe_set_spin"]
 
 
 class MBEError(RuntimeError):
@@ -77,6 +78,7 @@ def load_library(path: str = LIB_PATH):
     L.mbe_sigma_noalloc.argtypes = [vp, vp, c_int, vp, vp, ctypes.c_int64, vp]
     L.mbe_measure_peaks.argtypes = [c_int, vp, vp]
     L.mbe_set_pruning_pairs.argtypes = [vp, vp, c_int]
+    L.mbe_set_spin.argtypes = [vp, c_int]
     for name in EXPORTED:
         if name not in ("mbe_default_options", "mbe_destroy", "mbe_last_error",
                         "mbe_get_stats", "mbe_reset_stats", "mbe_set_order_energies",
@@ -232,8 +234,10 @@ class MBE:
         except Exception:
             pass
 
-    def load(self, h, eri, nelec):
+    def load(self, h, eri, nelec, two_sz=None):
         mbe_load_integrals(self.ctx, h, eri, nelec)
+        if two_sz is not None:
+            mbe_set_spin(self.ctx, two_sz)
         self.norb = h.shape[0]
 
     def run(self, ref, exp, max_order, thr=0.0, callback=None, pairs=None):
@@ -321,6 +325,11 @@ def mbe_measure_peaks(device: int = 0) -> dict:
     if rc != MBE_OK:
         raise MBEError(rc, "mbe_measure_peaks failed")
     return {"fp64_tflops": float(out[0]), "fp32_tflops": float(out[1])}
+
+
+def mbe_set_spin(ctx, two_sz: int):
+    """High-spin reference determinant with n_alpha - n_beta = two_sz (Fig. 2 (b))."""
+    return _check(ctx, load_library().mbe_set_spin(ctx, int(two_sz)))
 
 
 def mbe_set_pruning_pairs(ctx, pairs):

@@ -5,7 +5,7 @@ expansion (Eqs. 1-3) through the C ABI and returns the total energy as a
 0-d tensor whose backward calls ``mbe_energy_backward``: by Hellmann-Feynman
 each tuple energy is stationary in its CI coefficients, so the gradient is
 the MBE-weighted sum of the tuples' reduced density matrices, built on the
-GPU from the kept CI vectors.  ``h`` is (norb, norb) and ``eri`` the
+GPU from the kept RDMs.  ``h`` is (norb, norb) and ``eri`` the
 symmetric packed (npair, npair) matrix of (pq|rs); both float64 (any
 device; the library copies them).  The screening decisions (which tuples
 exist) are held fixed in the backward, as the energy is piecewise smooth in

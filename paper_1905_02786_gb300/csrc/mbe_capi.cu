@@ -1,6 +1,7 @@
 // C ABI of libmbe (declared in include/mbe.h): context, integrals, reference
 // space, batched CASCI solves, increments, tuple generation, gradient.
 #include "mbe_internal.cuh"
+#include <tuple>
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -119,6 +120,12 @@ StringTables* get_tables(mbe_ctx* ctx, int n, int nsig) {
 
 int count_sig(const mbe_ctx* ctx, const std::vector<int>& act) {
   int s = 0;
+  for (int a : act) s += a < ctx->nocc_a;
+  return s;
+}
+
+int count_sig_b(const mbe_ctx* ctx, const std::vector<int>& act) {
+  int s = 0;
   for (int a : act) s += a < ctx->nocc;
   return s;
 }
@@ -138,9 +145,12 @@ std::pair<uint64_t, uint64_t> orbital_key(const std::vector<int>& orbs) {
 // or the reference space as order 0); binned by (n, nsig).  With warm starts
 // on, a tuple whose parent (the tuple less one orbital) was solved at the
 // previous order starts from that vector, and the converged vectors of this
-// call are kept for the next order.
+// call are kept for the next order.  With rdm_out the packed RDMs of every
+// converged vector are formed on the device right after its batch (blocks
+// tagged with the order in ctx->rdm_blocks) and rdm_out[j] points at those
+// of acts[j]; no CI vector leaves the device.
 void solve_jobs(mbe_ctx* ctx, const std::vector<std::vector<int>>& acts, double* eps,
-                int32_t* status, std::vector<std::vector<double>>* ci_out, int order) {
+                int32_t* status, std::vector<const double*>* rdm_out, int order) {
   const bool warm = ctx->opt.warm_start != 0;
   if (warm) {
     if (ctx->guess_cur.order == order - 1) {
@@ -154,14 +164,16 @@ void solve_jobs(mbe_ctx* ctx, const std::vector<std::vector<int>>& acts, double*
   }
   std::vector<char> is_ref(ctx->norb, 0);
   for (int r : ctx->ref) is_ref[r] = 1;
-  std::map<std::pair<int, int>, std::vector<int64_t>> bins;
+  // bins: (n, alpha electrons, beta electrons); the two counts differ only
+  // for a high-spin reference
+  std::map<std::tuple<int, int, int>, std::vector<int64_t>> bins;
   for (int64_t j = 0; j < (int64_t)acts.size(); j++) {
     int n = (int)acts[j].size();
     if (n < 1 || n > MBE_MAX_ACT) throw MbeError{MBE_EINVAL, "active space size out of range"};
     if (n > 15) throw MbeError{MBE_EINVAL, "active spaces above 15 orbitals are not supported"};
-    bins[{n, count_sig(ctx, acts[j])}].push_back(j);
+    bins[{n, count_sig(ctx, acts[j]), count_sig_b(ctx, acts[j])}].push_back(j);
   }
-  if (ci_out) ci_out->assign(acts.size(), {});
+  if (rdm_out) rdm_out->assign(acts.size(), nullptr);
   size_t free_b = 0, total_b = 0;
   CU_CHECK(cudaMemGetInfo(&free_b, &total_b));
   // the pool's cached free blocks are reusable: they count as free
@@ -169,14 +181,18 @@ void solve_jobs(mbe_ctx* ctx, const std::vector<std::vector<int>>& acts, double*
   if (ctx->opt.mem_cap_bytes > 0) budget = std::min(budget, 0.5 * (double)ctx->opt.mem_cap_bytes);
   const int M = std::max(4, std::min(32, ctx->opt.max_subspace));
   for (auto& kv : bins) {
-    const int n = kv.first.first, nsig = kv.first.second;
+    const int n = std::get<0>(kv.first), nsig = std::get<1>(kv.first);
+    const int nsigb = std::get<2>(kv.first);
     StringTables* tab = get_tables(ctx, n, nsig);
-    const int64_t N = (int64_t)tab->nstr * tab->nstr;
+    StringTables* tabb = nsigb == nsig ? tab : get_tables(ctx, n, nsigb);
+    const bool closed = tabb == tab;
+    const int64_t N = (int64_t)tab->nstr * tabb->nstr;
     // device bytes per tuple: the mixed Davidson holds V and AV (M vectors
     // each) and five work vectors in FP32 plus two FP64 exact-point vectors,
     // the bf16 hi/lo copies of the sigma operand and of H^alpha and the
     // P-space eigenvectors; the FP64 one 2M + 6 FP64 vectors
-    const bool mixed_bin = ctx->opt.precision == MBE_MIXED_BF16X3 && N > 1 &&
+    // the mixed path works on alpha<->beta symmetric vectors: closed shells
+    const bool mixed_bin = ctx->opt.precision == MBE_MIXED_BF16X3 && N > 1 && closed &&
                            sigma_tc_supported(n, tab->nstr) && ozaki_supported(tab->npair);
     double per = (mixed_bin ? (double)(8 * M + 46) * N + 128.0 * 129.0 * 4.0
                             : (double)(2 * M + 6) * N * 8.0) +
@@ -194,6 +210,9 @@ void solve_jobs(mbe_ctx* ctx, const std::vector<std::vector<int>>& acts, double*
       bp.ndet = N;
       bp.B = B;
       bp.tab = tab;
+      bp.nsigb = nsigb;
+      bp.nstrb = tabb->nstr;
+      bp.tabb = tabb;
       std::vector<int32_t> act_h((size_t)B * n);
       for (int b = 0; b < B; b++)
         for (int i = 0; i < n; i++) act_h[(size_t)b * n + i] = acts[idx[c0 + b]][i];
@@ -202,8 +221,9 @@ void solve_jobs(mbe_ctx* ctx, const std::vector<std::vector<int>>& acts, double*
                                cudaMemcpyHostToDevice, ctx->stream));
       launch_effints(ctx, bp);
       // warm-start plan: the first parent found in the previous order's store
+      // (closed shells: the stored vectors are alpha<->beta symmetric)
       GuessPlan plan;
-      if (warm && order >= 1 && ctx->guess_prev.order == order - 1)
+      if (warm && closed && order >= 1 && ctx->guess_prev.order == order - 1)
         for (int b = 0; b < B; b++) {
           const std::vector<int>& act = acts[idx[c0 + b]];
           std::vector<int> tup;
@@ -224,13 +244,13 @@ void solve_jobs(mbe_ctx* ctx, const std::vector<std::vector<int>>& acts, double*
         }
       // keep this batch's vectors for the next order if they fit the cap
       const int64_t keep_bytes = (int64_t)B * N * 4;
-      const bool keep = warm && ctx->guess_cur.bytes + keep_bytes <= (int64_t)(0.25 * budget);
+      const bool keep =
+          warm && closed && ctx->guess_cur.bytes + keep_bytes <= (int64_t)(0.25 * budget);
       DevBuf<double> X;
-      if (ci_out || keep) X.reset(&ctx->pool, (size_t)B * N);
+      if (rdm_out || keep) X.reset(&ctx->pool, (size_t)B * N);
       std::vector<double> e(B);
       std::vector<int32_t> s(B);
-      const bool mixed = ctx->opt.precision == MBE_MIXED_BF16X3 && N > 1 &&
-                         sigma_tc_supported(n, tab->nstr) && ozaki_supported(tab->npair);
+      const bool mixed = mixed_bin;
       const GuessPlan* pp = plan.b.empty() ? nullptr : &plan;
       if (mixed)
         davidson_batch_mixed(ctx, bp, e.data(), s.data(), X.ptr, pp);
@@ -253,14 +273,12 @@ void solve_jobs(mbe_ctx* ctx, const std::vector<std::vector<int>>& acts, double*
         if (eps) eps[idx[c0 + b]] = e[b];
         if (status) status[idx[c0 + b]] = s[b];
       }
-      if (ci_out) {
-        for (int b = 0; b < B; b++) {
-          std::vector<double>& v = (*ci_out)[idx[c0 + b]];
-          v.resize(N);
-          CU_CHECK(cudaMemcpyAsync(v.data(), X.ptr + (int64_t)b * N, sizeof(double) * N,
-                                   cudaMemcpyDeviceToHost, ctx->stream));
-        }
-        CU_CHECK(cudaStreamSynchronize(ctx->stream));
+      if (rdm_out) {
+        const int64_t rs = rdm_size(tab->npair);
+        RdmBlock blk{order, std::make_unique<DevBuf<double>>(&ctx->pool, (size_t)(B * rs))};
+        rdm_batch(ctx, tab, tabb, X.ptr, B, mixed, blk.buf->ptr);
+        for (int b = 0; b < B; b++) (*rdm_out)[idx[c0 + b]] = blk.buf->ptr + b * rs;
+        ctx->rdm_blocks.push_back(std::move(blk));
       }
     }
   }
@@ -359,8 +377,8 @@ const char* mbe_last_error(const mbe_ctx* ctx) {
 int mbe_load_integrals(mbe_ctx* ctx, int norb, int nelec, const double* h, const double* eri) {
   return guarded(ctx, [&]() -> int {
     if (norb < 1 || norb > MBE_MAX_NORB) return fail(ctx, MBE_EINVAL, "norb out of range");
-    if (nelec < 0 || nelec % 2 || nelec / 2 > norb)
-      return fail(ctx, MBE_EINVAL, "nelec must be even and fit the orbitals");
+    if (nelec < 0 || (nelec + 1) / 2 > norb)
+      return fail(ctx, MBE_EINVAL, "nelec must fit the orbitals");
     if (!h || !eri) return fail(ctx, MBE_EINVAL, "null integral pointer");
     const int64_t np = (int64_t)norb * (norb + 1) / 2;
     for (int64_t i = 0; i < (int64_t)norb * norb; i++)
@@ -369,7 +387,10 @@ int mbe_load_integrals(mbe_ctx* ctx, int norb, int nelec, const double* h, const
       if (!std::isfinite(eri[i])) return fail(ctx, MBE_EINVAL, "non-finite eri");
     ctx->norb = norb;
     ctx->nelec = nelec;
-    ctx->nocc = nelec / 2;
+    // lowest spin of the high-spin family: singlet or doublet
+    ctx->two_sz = nelec % 2;
+    ctx->nocc = (nelec - ctx->two_sz) / 2;
+    ctx->nocc_a = ctx->nocc + ctx->two_sz;
     ctx->npair_g = (int)np;
     ctx->h_host.assign(h, h + (int64_t)norb * norb);
     ctx->eri_host.assign(eri, eri + np * np);
@@ -383,6 +404,30 @@ int mbe_load_integrals(mbe_ctx* ctx, int norb, int nelec, const double* h, const
     ctx->have_ref = false;
     ctx->kept.clear();
     ctx->kept_ref = false;
+    ctx->rdm_blocks.clear();
+    ctx->guess_prev.clear();
+    ctx->guess_cur.clear();
+    ctx->last_order = 0;
+    ctx->cur_order = 0;
+    ctx->order_sums.clear();
+    return MBE_OK;
+  });
+}
+
+int mbe_set_spin(mbe_ctx* ctx, int two_sz) {
+  return guarded(ctx, [&]() -> int {
+    if (ctx->norb == 0) return fail(ctx, MBE_ESTATE, "no integrals loaded");
+    if (two_sz < 0 || two_sz > ctx->nelec || (ctx->nelec - two_sz) % 2)
+      return fail(ctx, MBE_EINVAL, "two_sz must be in 0..nelec with the parity of nelec");
+    const int nb = (ctx->nelec - two_sz) / 2;
+    if (nb + two_sz > ctx->norb) return fail(ctx, MBE_EINVAL, "alpha electrons exceed the orbitals");
+    ctx->two_sz = two_sz;
+    ctx->nocc = nb;
+    ctx->nocc_a = nb + two_sz;
+    ctx->have_ref = false;
+    ctx->kept.clear();
+    ctx->kept_ref = false;
+    ctx->rdm_blocks.clear();
     ctx->guess_prev.clear();
     ctx->guess_cur.clear();
     ctx->last_order = 0;
@@ -404,6 +449,11 @@ int mbe_set_reference(mbe_ctx* ctx, const int* ref_orbs, int nref, const int* ex
       if (o < 0 || o >= ctx->norb || !seen.insert(o).second)
         return fail(ctx, MBE_EINVAL, "bad reference orbital");
     }
+    // a high-spin reference determinant: its singly occupied orbitals belong
+    // to the reference space (the inactive core stays closed-shell)
+    for (int o = ctx->nocc; o < ctx->nocc_a; o++)
+      if (!seen.count(o))
+        return fail(ctx, MBE_EINVAL, "singly occupied orbitals must be in the reference space");
     for (int i = 0; i < nexp; i++) {
       int o = exp_orbs[i];
       if (o < 0 || o >= ctx->norb || !seen.insert(o).second)
@@ -418,9 +468,12 @@ int mbe_set_reference(mbe_ctx* ctx, const int* ref_orbs, int nref, const int* ex
     ctx->guess_cur.clear();
     double e = 0.0;
     int32_t st = 0;
-    std::vector<std::vector<double>> ci;
+    std::vector<const double*> rdm;
+    ctx->kept.clear();
+    ctx->kept_ref = false;
+    ctx->rdm_blocks.clear();
     if (nref > 0) {
-      solve_jobs(ctx, {ctx->ref}, &e, &st, ctx->opt.keep_ci ? &ci : nullptr, 0);
+      solve_jobs(ctx, {ctx->ref}, &e, &st, ctx->opt.keep_ci ? &rdm : nullptr, 0);
     } else {
       // empty reference: the inactive-core energy of the closed-shell determinant
       double ec = 0.0;
@@ -438,14 +491,12 @@ int mbe_set_reference(mbe_ctx* ctx, const int* ref_orbs, int nref, const int* ex
     }
     ctx->e_ref = e;
     ctx->have_ref = true;
-    ctx->kept.clear();
-    ctx->kept_ref = false;
     if (ctx->opt.keep_ci && nref > 0) {
       ctx->ref_ci.order = 0;
       ctx->ref_ci.tuple.clear();
       ctx->ref_ci.n = nref;
       ctx->ref_ci.nsig = count_sig(ctx, ctx->ref);
-      ctx->ref_ci.c = std::move(ci[0]);
+      ctx->ref_ci.rdm = rdm[0];
       ctx->kept_ref = true;
     }
     hash_init(ctx, 4096);
@@ -482,8 +533,17 @@ int mbe_solve_tuples(mbe_ctx* ctx, int order, const int32_t* tuples, int64_t ntu
     }
     std::vector<double> eps(ntup);
     std::vector<int32_t> st(ntup, 0);
-    std::vector<std::vector<double>> ci;
-    solve_jobs(ctx, acts, eps.data(), st.data(), ctx->opt.keep_ci ? &ci : nullptr, order);
+    std::vector<const double*> rdm;
+    if (ctx->opt.keep_ci) {
+      // a re-solve of this order replaces the RDMs kept for it and above
+      ctx->kept.erase(std::remove_if(ctx->kept.begin(), ctx->kept.end(),
+                                     [&](const KeptRdm& k) { return k.order >= order; }),
+                      ctx->kept.end());
+      ctx->rdm_blocks.erase(std::remove_if(ctx->rdm_blocks.begin(), ctx->rdm_blocks.end(),
+                                           [&](const RdmBlock& b) { return b.order >= order; }),
+                            ctx->rdm_blocks.end());
+    }
+    solve_jobs(ctx, acts, eps.data(), st.data(), ctx->opt.keep_ci ? &rdm : nullptr, order);
     ctx->cur_order = order;
     ctx->cur_tuples.assign(tuples, tuples + ntup * order);
     ctx->cur_eps = eps;
@@ -497,17 +557,13 @@ int mbe_solve_tuples(mbe_ctx* ctx, int order, const int32_t* tuples, int64_t ntu
       CU_CHECK(cudaStreamSynchronize(ctx->stream));
     }
     if (ctx->opt.keep_ci) {
-      // replace previously kept vectors of this order (a re-solve)
-      ctx->kept.erase(std::remove_if(ctx->kept.begin(), ctx->kept.end(),
-                                     [&](const KeptCI& k) { return k.order >= order; }),
-                      ctx->kept.end());
       for (int64_t t = 0; t < ntup; t++) {
-        KeptCI k;
+        KeptRdm k;
         k.order = order;
         k.tuple.assign(tuples + t * order, tuples + (t + 1) * order);
         k.n = (int)acts[t].size();
         k.nsig = count_sig(ctx, acts[t]);
-        k.c = std::move(ci[t]);
+        k.rdm = rdm[t];
         ctx->kept.push_back(std::move(k));
       }
     }
@@ -756,16 +812,23 @@ int mbe_sigma(mbe_ctx* ctx, const int* act, int nact, const double* c, double* s
     for (int i = 0; i < nact; i++)
       if (a[i] < 0 || a[i] >= ctx->norb || (i && a[i] == a[i - 1]))
         return fail(ctx, MBE_EINVAL, "bad active orbital");
-    const int nsig = count_sig(ctx, a);
+    for (int o = ctx->nocc; o < ctx->nocc_a; o++)
+      if (!std::binary_search(a.begin(), a.end(), o))
+        return fail(ctx, MBE_EINVAL, "singly occupied orbitals must be active");
+    const int nsig = count_sig(ctx, a), nsigb = count_sig_b(ctx, a);
     StringTables* tab = get_tables(ctx, nact, nsig);
+    StringTables* tabb = nsigb == nsig ? tab : get_tables(ctx, nact, nsigb);
     BinProblem bp;
     bp.n = nact;
     bp.nsig = nsig;
     bp.nstr = tab->nstr;
     bp.npair = tab->npair;
-    bp.ndet = (int64_t)tab->nstr * tab->nstr;
+    bp.nsigb = nsigb;
+    bp.nstrb = tabb->nstr;
+    bp.ndet = (int64_t)tab->nstr * tabb->nstr;
     bp.B = 1;
     bp.tab = tab;
+    bp.tabb = tabb;
     bp.act.reset(&ctx->pool, nact);
     std::vector<int32_t> a32(a.begin(), a.end());
     CU_CHECK(cudaMemcpyAsync(bp.act.ptr, a32.data(), sizeof(int32_t) * nact, cudaMemcpyHostToDevice,
@@ -776,8 +839,8 @@ int mbe_sigma(mbe_ctx* ctx, const int* act, int nact, const double* c, double* s
                              ctx->stream));
     SigmaWork w;
     // mixed precision: the tensor-core path (valid for c = c^T, the
-    // alpha<->beta symmetric sector), else FP64
-    if (ctx->opt.precision == MBE_MIXED_BF16X3 && sigma_tc_supported(nact, bp.nstr)) {
+    // alpha<->beta symmetric sector of a closed shell), else FP64
+    if (ctx->opt.precision == MBE_MIXED_BF16X3 && bp.closed() && sigma_tc_supported(nact, bp.nstr)) {
       // the mixed mode keeps its vectors in FP32
       std::vector<float> cf(c, c + bp.ndet), sf(bp.ndet);
       DevBuf<float> cdf(&ctx->pool, bp.ndet), sdf(&ctx->pool, bp.ndet);
@@ -797,7 +860,7 @@ int mbe_sigma(mbe_ctx* ctx, const int* act, int nact, const double* c, double* s
       // emulated FP64: the fused exact kernel for vectors like the mixed
       // mode's exact points (c = c^T with FP32 values, |c_i| <= 1), else the
       // sliced contraction on HBM intermediates
-      bool fused = ctx->opt.precision == MBE_EMULATED_FP64 &&
+      bool fused = ctx->opt.precision == MBE_EMULATED_FP64 && bp.closed() &&
                    sigma_exact_supported(bp.npair, bp.nstr);
       for (int64_t i = 0; fused && i < bp.nstr; i++)
         for (int64_t j = 0; j <= i; j++) {

@@ -257,8 +257,11 @@ __device__ __forceinline__ double string_self(uint32_t m, const double* heff, co
   return e + 0.5 * e2;
 }
 
-// <Ia Ib| H_active + shift S^2 |Ia Ib>, computed symmetrically in (Ia, Ib)
-__global__ void k_hdiag(const uint32_t* __restrict__ masks, int nstr, int n, int nsig,
+// <Ia Ib| H_active + shift S^2 |Ia Ib>, computed symmetrically in (Ia, Ib).
+// alpha strings masks[nstr], beta strings masksb[nstrb] (the same table for
+// a closed shell); <S^2> diagonal = (beta-only orbitals) + Ms(Ms+1) (msms).
+__global__ void k_hdiag(const uint32_t* __restrict__ masks, const uint32_t* __restrict__ masksb,
+                        int nstr, int nstrb, int n, int nsigb, double msms,
                         const double* __restrict__ heff_all, const double* __restrict__ jk_all,
                         double shift, double* hd_all) {
   const int b = blockIdx.y;
@@ -272,11 +275,11 @@ __global__ void k_hdiag(const uint32_t* __restrict__ masks, int nstr, int n, int
     s_K[t] = jk_all[(int64_t)b * 2 * n * n + n * n + t];
   }
   __syncthreads();
-  const int64_t ndet = (int64_t)nstr * nstr;
+  const int64_t ndet = (int64_t)nstr * nstrb;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndet;
        i += (int64_t)gridDim.x * blockDim.x) {
-    int ia = (int)(i / nstr), ib = (int)(i % nstr);
-    uint32_t ma = masks[ia], mb = masks[ib];
+    int ia = (int)(i / nstrb), ib = (int)(i % nstrb);
+    uint32_t ma = masks[ia], mb = masksb[ib];
     double ea = string_self(ma, s_heff, s_J, s_K, n);
     double eb = string_self(mb, s_heff, s_J, s_K, n);
     double cross = 0.0;
@@ -289,7 +292,7 @@ __global__ void k_hdiag(const uint32_t* __restrict__ masks, int nstr, int n, int
       }
     }
     int ndocc = __popc(ma & mb);
-    hd_all[(int64_t)b * ndet + i] = (ea + eb) + cross + shift * (double)(nsig - ndocc);
+    hd_all[(int64_t)b * ndet + i] = (ea + eb) + cross + shift * ((double)(nsigb - ndocc) + msms);
   }
 }
 
@@ -301,8 +304,9 @@ void launch_hdiag(mbe_ctx* ctx, BinProblem& bp, double spin_shift, double* hd) {
   int64_t blocks = (bp.ndet + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   dim3 grid((unsigned)blocks, bp.B);
-  k_hdiag<<<grid, 256, smem, ctx->stream>>>(bp.tab->masks.ptr, bp.nstr, n, bp.nsig,
-                                            bp.heff.ptr, bp.jk.ptr, spin_shift, hd);
+  k_hdiag<<<grid, 256, smem, ctx->stream>>>(bp.tab->masks.ptr, bp.tabb->masks.ptr, bp.nstr,
+                                            bp.nstrb, n, bp.nsigb, bp.msms(), bp.heff.ptr,
+                                            bp.jk.ptr, spin_shift, hd);
   CU_LAUNCH_CHECK();
 }
 
@@ -310,7 +314,8 @@ void launch_hdiag(mbe_ctx* ctx, BinProblem& bp, double spin_shift, double* hd) {
 namespace {
 
 // D[b][P][Ia*nstr+Ib] = s_a C(Ja, Ib) + s_b C(Ia, Jb)
-__global__ void k_gather_fp64(const int32_t* __restrict__ link, int nstr, int npair,
+__global__ void k_gather_fp64(const int32_t* __restrict__ link, const int32_t* __restrict__ linkb,
+                              int nstr, int nstrb, int npair,
                               const double* __restrict__ c, int64_t c_stride,
                               const int32_t* __restrict__ active, const int32_t* __restrict__ bmap,
                               double* __restrict__ D) {
@@ -318,22 +323,22 @@ __global__ void k_gather_fp64(const int32_t* __restrict__ link, int nstr, int np
   const int b = bmap[bl];
   if (active && !active[b]) return;
   const double* cb = c + (int64_t)b * c_stride;
-  const int64_t ndet = (int64_t)nstr * nstr;
+  const int64_t ndet = (int64_t)nstr * nstrb;
   double* Db = D + (int64_t)bl * npair * ndet;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndet;
        i += (int64_t)gridDim.x * blockDim.x) {
-    int ia = (int)(i / nstr), ib = (int)(i % nstr);
+    int ia = (int)(i / nstrb), ib = (int)(i % nstrb);
     const int32_t* la = link + (int64_t)ia * npair;
-    const int32_t* lb = link + (int64_t)ib * npair;
+    const int32_t* lb = linkb + (int64_t)ib * npair;
     for (int P = 0; P < npair; P++) {
       double v = 0.0;
       int32_t ta = la[P], tb = lb[P];
       if (ta >= 0) {
-        double x = cb[(int64_t)(ta >> 1) * nstr + ib];
+        double x = cb[(int64_t)(ta >> 1) * nstrb + ib];
         v += (ta & 1) ? -x : x;
       }
       if (tb >= 0) {
-        double x = cb[(int64_t)ia * nstr + (tb >> 1)];
+        double x = cb[(int64_t)ia * nstrb + (tb >> 1)];
         v += (tb & 1) ? -x : x;
       }
       Db[(int64_t)P * ndet + i] = v;
@@ -410,8 +415,14 @@ __device__ __forceinline__ double load_e(const double* __restrict__ Eb, int64_t 
   return (double)v.x + (double)v.y;
 }
 
+// General (not necessarily symmetric) c, alpha table link/masks (nstr
+// strings) and beta table linkb/masksb (nstrb strings, the same table for a
+// closed shell); S^2 = S-S+ + Ms(Ms+1): diagonal (beta-only orbitals) + msms,
+// off-diagonal the alpha-only / beta-only exchanges.
 __global__ void k_scatter_fp64(const int32_t* __restrict__ link, const uint32_t* __restrict__ masks,
-                               int nstr, int n, int nsig, const double* __restrict__ E, int pair_e,
+                               const int32_t* __restrict__ linkb,
+                               const uint32_t* __restrict__ masksb, int nstr, int nstrb, int n,
+                               int nsigb, double msms, const double* __restrict__ E, int pair_e,
                                const double* __restrict__ c, int64_t c_stride, double shift,
                                const int32_t* __restrict__ active, const int32_t* __restrict__ bmap,
                                double* __restrict__ out, int64_t out_stride) {
@@ -419,31 +430,31 @@ __global__ void k_scatter_fp64(const int32_t* __restrict__ link, const uint32_t*
   const int b = bmap[bl];
   if (active && !active[b]) return;
   const int npair = n * (n + 1) / 2;
-  const int64_t ndet = (int64_t)nstr * nstr;
+  const int64_t ndet = (int64_t)nstr * nstrb;
   const double* Eb = E + (int64_t)bl * npair * ndet;
   const double* cb = c + (int64_t)b * c_stride;
   double* ob = out + (int64_t)b * out_stride;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndet;
        i += (int64_t)gridDim.x * blockDim.x) {
-    int ia = (int)(i / nstr), ib = (int)(i % nstr);
+    int ia = (int)(i / nstrb), ib = (int)(i % nstrb);
     const int32_t* la = link + (int64_t)ia * npair;
-    const int32_t* lb = link + (int64_t)ib * npair;
+    const int32_t* lb = linkb + (int64_t)ib * npair;
     double acc = 0.0;
     for (int P = 0; P < npair; P++) {
       int32_t ta = la[P], tb = lb[P];
       if (ta >= 0) {
-        double x = load_e(Eb, (int64_t)P * ndet + (int64_t)(ta >> 1) * nstr + ib, pair_e);
+        double x = load_e(Eb, (int64_t)P * ndet + (int64_t)(ta >> 1) * nstrb + ib, pair_e);
         acc += (ta & 1) ? -x : x;
       }
       if (tb >= 0) {
-        double x = load_e(Eb, (int64_t)P * ndet + (int64_t)ia * nstr + (tb >> 1), pair_e);
+        double x = load_e(Eb, (int64_t)P * ndet + (int64_t)ia * nstrb + (tb >> 1), pair_e);
         acc += (tb & 1) ? -x : x;
       }
     }
     double v = 0.5 * acc;
     if (shift != 0.0) {
-      uint32_t ma = masks[ia], mb = masks[ib];
-      double s2 = (double)(nsig - __popc(ma & mb)) * cb[i];
+      uint32_t ma = masks[ia], mb = masksb[ib];
+      double s2 = ((double)(nsigb - __popc(ma & mb)) + msms) * cb[i];
       uint32_t oa = ma & ~mb, ob2 = mb & ~ma;   // open shells of each spin
       for (int q = 0; q < n; q++) {
         if (!((oa >> q) & 1)) continue;
@@ -451,7 +462,7 @@ __global__ void k_scatter_fp64(const int32_t* __restrict__ link, const uint32_t*
           if (!((ob2 >> p) & 1)) continue;
           int P = p > q ? p * (p + 1) / 2 + q : q * (q + 1) / 2 + p;
           int32_t ta = la[P], tb = lb[P];
-          double x = cb[(int64_t)(ta >> 1) * nstr + (tb >> 1)];
+          double x = cb[(int64_t)(ta >> 1) * nstrb + (tb >> 1)];
           s2 -= ((ta ^ tb) & 1) ? -x : x;
         }
       }
@@ -559,22 +570,24 @@ __global__ void k_finish_sym_fp64(double* __restrict__ out, int64_t out_stride,
 }
 
 __global__ void k_s2(const int32_t* __restrict__ link, const uint32_t* __restrict__ masks,
-                     int nstr, int n, int nsig, const double* __restrict__ c, int64_t c_stride,
+                     const int32_t* __restrict__ linkb, const uint32_t* __restrict__ masksb,
+                     int nstr, int nstrb, int n, int nsigb, double msms,
+                     const double* __restrict__ c, int64_t c_stride,
                      const int32_t* __restrict__ active, double* __restrict__ out,
                      int64_t out_stride) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
   const int npair = n * (n + 1) / 2;
-  const int64_t ndet = (int64_t)nstr * nstr;
+  const int64_t ndet = (int64_t)nstr * nstrb;
   const double* cb = c + (int64_t)b * c_stride;
   double* ob = out + (int64_t)b * out_stride;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ndet;
        i += (int64_t)gridDim.x * blockDim.x) {
-    int ia = (int)(i / nstr), ib = (int)(i % nstr);
+    int ia = (int)(i / nstrb), ib = (int)(i % nstrb);
     const int32_t* la = link + (int64_t)ia * npair;
-    const int32_t* lb = link + (int64_t)ib * npair;
-    uint32_t ma = masks[ia], mb = masks[ib];
-    double s2 = (double)(nsig - __popc(ma & mb)) * cb[i];
+    const int32_t* lb = linkb + (int64_t)ib * npair;
+    uint32_t ma = masks[ia], mb = masksb[ib];
+    double s2 = ((double)(nsigb - __popc(ma & mb)) + msms) * cb[i];
     uint32_t oa = ma & ~mb, obm = mb & ~ma;
     for (int q = 0; q < n; q++) {
       if (!((oa >> q) & 1)) continue;
@@ -582,7 +595,7 @@ __global__ void k_s2(const int32_t* __restrict__ link, const uint32_t* __restric
         if (!((obm >> p) & 1)) continue;
         int P = p > q ? p * (p + 1) / 2 + q : q * (q + 1) / 2 + p;
         int32_t ta = la[P], tb = lb[P];
-        double x = cb[(int64_t)(ta >> 1) * nstr + (tb >> 1)];
+        double x = cb[(int64_t)(ta >> 1) * nstrb + (tb >> 1)];
         s2 -= ((ta ^ tb) & 1) ? -x : x;
       }
     }
@@ -620,7 +633,8 @@ void sigma_fp64(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const double* c, int
     const int nb = (int)std::min<int64_t>(sb, bp.B - b0);
     sigma_fp64_raw(ctx, bp.n, bp.nsig, bp.nstr, bp.tab->link.ptr, bp.tab->masks.ptr, bp.gp.ptr, c,
                    c_stride, out, out_stride, active, bmap.ptr + b0, nb, w.D.ptr, w.E.ptr,
-                   spin_shift, emulated, w.err.ptr, symmetric, (int)b0);
+                   spin_shift, emulated, w.err.ptr, symmetric && bp.closed(), (int)b0, bp.nsigb,
+                   bp.nstrb, bp.tabb->link.ptr, bp.tabb->masks.ptr);
   }
 }
 
@@ -628,9 +642,17 @@ void sigma_fp64_raw(mbe_ctx* ctx, int n, int nsig, int nstr, const int32_t* link
                     const uint32_t* masks, const double* gp, const double* c, int64_t c_stride,
                     double* out, int64_t out_stride, const int32_t* active, const int32_t* bmap,
                     int nb, double* D, double* E, double spin_shift, bool emulated, int32_t* err,
-                    bool symmetric, int b_first) {
+                    bool symmetric, int b_first, int nsigb, int nstrb, const int32_t* linkb,
+                    const uint32_t* masksb) {
+  if (nsigb < 0) {   // closed shell: beta strings = alpha strings
+    nsigb = nsig;
+    nstrb = nstr;
+    linkb = link;
+    masksb = masks;
+  }
+  const double msms = 0.25 * (nsig - nsigb) * (nsig - nsigb + 2);   // Ms(Ms+1)
   const int npair = n * (n + 1) / 2;
-  const int64_t ndet = (int64_t)nstr * nstr;
+  const int64_t ndet = (int64_t)nstr * nstrb;
   int64_t blocks = (ndet + 255) / 256;
   if (blocks > 2048) blocks = 2048;
   const size_t smem_c = sizeof(double) * (npair * npair + npair * GT_N);
@@ -642,7 +664,8 @@ void sigma_fp64_raw(mbe_ctx* ctx, int n, int nsig, int nstr, const int32_t* link
   int64_t cblocks = (ndet + GT_N - 1) / GT_N;
   if (cblocks > 1024) cblocks = 1024;
   const dim3 g1((unsigned)blocks, nb);
-  k_gather_fp64<<<g1, 256, 0, ctx->stream>>>(link, nstr, npair, c, c_stride, active, bmap, D);
+  k_gather_fp64<<<g1, 256, 0, ctx->stream>>>(link, linkb, nstr, nstrb, npair, c, c_stride, active,
+                                              bmap, D);
   CU_LAUNCH_CHECK();
   cudaEvent_t ev;
   ctx->fp64_timer.begin(ctx->stream, ctx->opt.timing != 0, &ev);
@@ -667,9 +690,9 @@ void sigma_fp64_raw(mbe_ctx* ctx, int n, int nsig, int nstr, const int32_t* link
         c + (int64_t)b0 * c_stride, c_stride, spin_shift, active ? active + b0 : nullptr);
     CU_LAUNCH_CHECK();
   } else {
-    k_scatter_fp64<<<g1, 256, 0, ctx->stream>>>(link, masks, nstr, n, nsig, E, emulated ? 1 : 0,
-                                                c, c_stride, spin_shift, active, bmap, out,
-                                                out_stride);
+    k_scatter_fp64<<<g1, 256, 0, ctx->stream>>>(link, masks, linkb, masksb, nstr, nstrb, n, nsigb,
+                                                msms, E, emulated ? 1 : 0, c, c_stride,
+                                                spin_shift, active, bmap, out, out_stride);
     CU_LAUNCH_CHECK();
   }
 }
@@ -679,19 +702,9 @@ void s2_apply(mbe_ctx* ctx, BinProblem& bp, const double* c, int64_t c_stride, d
   int64_t blocks = (bp.ndet + 255) / 256;
   if (blocks > 2048) blocks = 2048;
   dim3 g((unsigned)blocks, bp.B);
-  k_s2<<<g, 256, 0, ctx->stream>>>(bp.tab->link.ptr, bp.tab->masks.ptr, bp.nstr, bp.n, bp.nsig, c,
-                                   c_stride, active, out, out_stride);
-  CU_LAUNCH_CHECK();
-}
-
-void gather_d_fp64(mbe_ctx* ctx, const StringTables* tab, const double* c, double* D) {
-  const int64_t ndet = (int64_t)tab->nstr * tab->nstr;
-  DevBuf<int32_t> bmap(&ctx->pool, 1);
-  CU_CHECK(cudaMemsetAsync(bmap.ptr, 0, sizeof(int32_t), ctx->stream));
-  int64_t blocks = (ndet + 255) / 256;
-  if (blocks > 2048) blocks = 2048;
-  k_gather_fp64<<<dim3((unsigned)blocks, 1), 256, 0, ctx->stream>>>(
-      tab->link.ptr, tab->nstr, tab->npair, c, ndet, nullptr, bmap.ptr, D);
+  k_s2<<<g, 256, 0, ctx->stream>>>(bp.tab->link.ptr, bp.tab->masks.ptr, bp.tabb->link.ptr,
+                                   bp.tabb->masks.ptr, bp.nstr, bp.nstrb, bp.n, bp.nsigb,
+                                   bp.msms(), c, c_stride, active, out, out_stride);
   CU_LAUNCH_CHECK();
 }
 

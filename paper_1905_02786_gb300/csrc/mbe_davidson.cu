@@ -268,17 +268,28 @@ __global__ void k_save_yprev(const double* __restrict__ y, int m, int M, int res
     yp[(int64_t)b * M + i] = restarted ? (i == 0 ? 1.0 : 0.0) : (i < m ? y[(int64_t)b * M + i] : 0.0);
 }
 
-// t = r / (theta - H_II), then t <- (t + t^T)/2 so that every subspace
-// vector stays exactly in the alpha<->beta symmetric (even-S) sector; each
-// thread owns the pair (Ia,Ib), (Ib,Ia) with Ia <= Ib.
+// t = r / (theta - H_II), then (closed shell, nstrb < 0) t <- (t + t^T)/2
+// so that every subspace vector stays exactly in the alpha<->beta symmetric
+// (even-S) sector; each thread owns the pair (Ia,Ib), (Ib,Ia) with Ia <= Ib.
+// A high-spin space (nstrb >= 0 beta strings) has no such symmetry.
 __global__ void k_precondition(double* __restrict__ T, const double* __restrict__ hd, int nstr,
-                               const double* __restrict__ theta, const int32_t* __restrict__ active) {
+                               int nstrb, const double* __restrict__ theta,
+                               const int32_t* __restrict__ active) {
   const int b = blockIdx.y;
   if (!active[b]) return;
   const double th = theta[b];
-  const int64_t N = (int64_t)nstr * nstr;
+  const int64_t N = (int64_t)nstr * (nstrb < 0 ? nstr : nstrb);
   double* Tb = T + (int64_t)b * N;
   const double* hb = hd + (int64_t)b * N;
+  if (nstrb >= 0) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N;
+         k += (int64_t)gridDim.x * blockDim.x) {
+      double d = th - hb[k];
+      if (fabs(d) < 1e-8) d = d < 0.0 ? -1e-8 : 1e-8;
+      Tb[k] = Tb[k] / d;
+    }
+    return;
+  }
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int ia = (int)(k / nstr), ib = (int)(k % nstr);
@@ -333,10 +344,13 @@ __global__ void k_fix_frozen(int32_t* active, int B) {
     if (active[b] == 2) active[b] = 0;
 }
 
-// start vector: lowest diagonal determinant (Ia, Ib), symmetrised
-__global__ void k_guess(const double* __restrict__ hd, int nstr, int M, double* __restrict__ V) {
+// start vector: lowest diagonal determinant (Ia, Ib), symmetrised for a
+// closed shell (nstrb < 0); for a high-spin space (nstrb beta strings) the
+// determinant itself
+__global__ void k_guess(const double* __restrict__ hd, int nstr, int nstrb, int M,
+                        double* __restrict__ V) {
   const int b = blockIdx.x;
-  const int64_t N = (int64_t)nstr * nstr;
+  const int64_t N = (int64_t)nstr * (nstrb < 0 ? nstr : nstrb);
   __shared__ double sv[256];
   __shared__ int64_t si[256];
   double best = 1e300;
@@ -365,7 +379,7 @@ __global__ void k_guess(const double* __restrict__ hd, int nstr, int M, double* 
   if (threadIdx.x == 0) {
     int64_t i0 = si[0];
     int ia = (int)(i0 / nstr), ib = (int)(i0 % nstr);
-    if (ia == ib) Vb[i0] = 1.0;
+    if (nstrb >= 0 || ia == ib) Vb[i0] = 1.0;
     else {
       Vb[(int64_t)ia * nstr + ib] = sqrt(0.5);
       Vb[(int64_t)ib * nstr + ia] = sqrt(0.5);
@@ -426,7 +440,8 @@ void davidson_batch(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int32_t* s
   const bool emulated = ctx->opt.precision != MBE_FP64 && ozaki_supported(bp.npair);
 
   launch_hdiag(ctx, bp, shift, hd.ptr);
-  k_guess<<<B, 256, 0, st>>>(hd.ptr, bp.nstr, M, V.ptr);
+  const int nstrb_arg = bp.closed() ? -1 : bp.nstrb;
+  k_guess<<<B, 256, 0, st>>>(hd.ptr, bp.nstr, nstrb_arg, M, V.ptr);
   CU_LAUNCH_CHECK();
   if (plan) launch_parent_guess(ctx, *plan, bp.n, bp.nsig, bp.nstr, nullptr, V.ptr, (int64_t)M * N);
   k_set_i32<<<1, 256, 0, st>>>(active.ptr, B, 1);
@@ -451,7 +466,7 @@ void davidson_batch(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int32_t* s
   // precondition the residual in T, orthogonalise it against V[0..m) and
   // append it as V[m] (tuples whose correction vanished are frozen)
   auto extend = [&](int m) {
-    k_precondition<<<ge, 256, 0, st>>>(T.ptr, hd.ptr, bp.nstr, theta.ptr, active.ptr);
+    k_precondition<<<ge, 256, 0, st>>>(T.ptr, hd.ptr, bp.nstr, nstrb_arg, theta.ptr, active.ptr);
     CU_LAUNCH_CHECK();
     for (int pass = 0; pass < 2; pass++) {
       md.run(ctx, V.ptr, (int64_t)M * N, N, T.ptr, N, m, N, B, active.ptr, coef.ptr, M, 1);

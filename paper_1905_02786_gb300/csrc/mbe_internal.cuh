@@ -142,12 +142,27 @@ struct StringTables {
 };
 
 // ------------------------------------------------------------- context
-struct KeptCI {
+// Spin-summed active-space RDMs of one converged CASCI, kept on the device
+// for the energy backward (keep_ci): gamma+_P = <c|E+_P|c> for the npair
+// packed pairs, then the upper triangle (P <= Q, row by row) of
+// Gamma'_PQ = <E+_P c, E+_Q c>, both for the normalised vector.
+struct KeptRdm {
   int order;
   std::vector<int32_t> tuple;  // global orbital ids of the tuple
   int n, nsig;
-  std::vector<double> c;       // converged CI vector (nstr*nstr), host copy
+  const double* rdm = nullptr; // rdm_size(npair) doubles inside a RdmBlock
 };
+struct RdmBlock {
+  int order;
+  std::unique_ptr<DevBuf<double>> buf;
+};
+inline int64_t rdm_size(int npair) { return npair + (int64_t)npair * (npair + 1) / 2; }
+// packed RDMs (rdm_size(tab->npair) doubles per vector, into out) of the B
+// converged vectors X (B * nstr_alpha * nstr_beta, FP64; alpha strings tab,
+// beta strings tabb); fp32: products and the sums inside a tile in FP32
+// (vectors of the mixed path), else FP64 throughout
+void rdm_batch(mbe_ctx* ctx, const StringTables* tab, const StringTables* tabb, const double* X,
+               int B, bool fp32, double* out);
 
 struct HashTable {
   int64_t cap = 0;             // power of two
@@ -207,7 +222,9 @@ struct mbe_ctx {
   DevPool pool;
 
   // integrals
-  int norb = 0, nelec = 0, nocc = 0, npair_g = 0;
+  // nocc: doubly occupied orbitals of the reference determinant (the beta
+  // occupation); nocc_a = nocc + two_sz: alpha occupation (high spin)
+  int norb = 0, nelec = 0, nocc = 0, npair_g = 0, nocc_a = 0, two_sz = 0;
   DevBuf<double> h, eri;
   std::vector<double> h_host, eri_host;
 
@@ -232,10 +249,11 @@ struct mbe_ctx {
   int prev_order = 0;
   std::vector<double> order_sums;
   std::vector<OrderRec> history;      // every processed order
-  // all processed tuples (for the backward): order, tuple, kept CI
-  std::vector<KeptCI> kept;
+  // all solved tuples (for the backward): order, tuple, kept RDMs
+  std::vector<KeptRdm> kept;
   bool kept_ref = false;
-  KeptCI ref_ci;
+  KeptRdm ref_ci;
+  std::vector<RdmBlock> rdm_blocks;
   // warm-start vectors of the previous and the current order
   GuessStore guess_prev, guess_cur;
   // pi-pruning: partner[o] = the degenerate partner of expansion orbital o
@@ -249,10 +267,21 @@ struct mbe_ctx {
 
 // ------------------------------------------------- per-bin solver state
 struct BinProblem {
-  int n, nsig, nstr, npair;
-  int64_t ndet;
+  int n, nsig, nstr, npair;      // nsig, nstr: alpha electrons and strings
+  int nsigb = -1, nstrb = -1;    // beta electrons and strings
+  int64_t ndet;                  // nstr * nstrb
   int B;                         // tuples in this batch
-  const StringTables* tab;
+  const StringTables* tab;       // alpha strings
+  const StringTables* tabb = nullptr;   // beta strings (== tab for a closed shell)
+  bool closed() const { return tabb == tab; }
+  // Ms(Ms+1) of every determinant of the space, Ms = (nsig - nsigb) / 2
+  double msms() const { return 0.25 * (nsig - nsigb) * (nsig - nsigb + 2); }
+  // beta side = alpha side (closed shell)
+  void set_closed() {
+    nsigb = nsig;
+    nstrb = nstr;
+    tabb = tab;
+  }
   DevBuf<int32_t> act;           // B * n global orbital ids
   DevBuf<double> ecore;          // B
   DevBuf<double> heff;           // B * n * n
@@ -296,11 +325,13 @@ void sigma_fp64_raw(mbe_ctx* ctx, int n, int nsig, int nstr, const int32_t* link
                     const uint32_t* masks, const double* gp, const double* c, int64_t c_stride,
                     double* out, int64_t out_stride, const int32_t* active, const int32_t* bmap,
                     int nb, double* D, double* E, double spin_shift, bool emulated, int32_t* err,
-                    bool symmetric = false, int b_first = 0);
+                    bool symmetric = false, int b_first = 0, int nsigb = -1, int nstrb = -1,
+                    const int32_t* linkb = nullptr, const uint32_t* masksb = nullptr);
 StringTables* get_tables(mbe_ctx* ctx, int n, int nsig);
+// active electrons of each spin: alpha (orbitals below nocc_a), beta (below nocc)
 int count_sig(const mbe_ctx* ctx, const std::vector<int>& act);
+int count_sig_b(const mbe_ctx* ctx, const std::vector<int>& act);
 // D[P][K] = (E+_P c)(K) for one CI vector c (ndet) and every packed pair P
-void gather_d_fp64(mbe_ctx* ctx, const StringTables* tab, const double* c, double* D);
 // mbe_sigma_noalloc (scratch in a file-scope device array)
 int noalloc_sigma_run(mbe_ctx* ctx, const int* act, int nact, const double* c_dev,
                       double* sigma_dev, int64_t ndet_arg, double* e_core);

@@ -96,6 +96,8 @@ int noalloc_sigma_run(mbe_ctx* ctx, const int* act, int nact, const double* c_de
   if (ctx->norb == 0) throw MbeError{MBE_ESTATE, "no integrals loaded"};
   if (nact < 1 || nact > 15 || !act || !c_dev || !sigma_dev)
     throw MbeError{MBE_EINVAL, "bad sigma arguments"};
+  if (ctx->two_sz != 0)
+    throw MbeError{MBE_EINVAL, "the no-allocation sigma takes closed-shell references only"};
   std::vector<int32_t> a(act, act + nact);
   std::sort(a.begin(), a.end());
   for (int i = 0; i < nact; i++)

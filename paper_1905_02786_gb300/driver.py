@@ -144,10 +144,10 @@ def run_expansion(ctx, ref, exp, max_order, thr=0.0, rank=0, world=1, allgather=
 
 
 def sharded_backward(ctx, norb, rank=0, world=1, allreduce=None, api=None):
-    """Gradient of a sharded expansion: each context sums the RDMs of the CI
-    vectors it holds (created with backward_share = 2 on rank 0 and 1 on the
-    others, so the reference term is counted once) and the shares are summed
-    over the ranks."""
+    """Gradient of a sharded expansion: each context sums the weighted RDMs
+    of the CASCIs it solved (created with backward_share = 2 on rank 0 and 1
+    on the others, so the reference term is counted once) and the shares are
+    summed over the ranks."""
     B_ = api or B
     dh, deri = B_.mbe_energy_backward(ctx, norb)
     if world > 1:

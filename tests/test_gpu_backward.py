@@ -224,3 +224,29 @@ def test_grad_workload_fd_sample(lib):
         fd = (energy(h, ep) - energy(h, em)) / (2 * step)
         an = dg[a, b] * (1 if a == b else 2)
         assert abs(fd - an) <= 1e-6 * abs(an) + 2e-7, (a, b, fd, an)
+
+
+def test_backward_mixed_path_matches_oracle(lib):
+    """The backward of the mixed-precision path (the production workload asks
+    for it there).  Its RDMs come from the FP32 exact-point vectors, converged
+    to the mixed path's relative residual (mixed_rel_tol, 2e-7); an RDM is
+    first order in the vector error (residual / gap), so each CASCI carries
+    ~1e-6 relative error, and the MBE coefficients of an order-3 expansion over
+    8 orbitals (|c_T| up to 35) add those of ~100 CASCIs.  Bound: 2e-5 of the
+    largest gradient entry (measured 6e-6 and 7e-6 of it; the FP64 path meets
+    1e-9 absolute)."""
+    norb, nocc, seed = 10, 3, 5
+    ref, exp = [2, 3], [0, 1, 4, 5, 6, 7, 8, 9]
+    h, eri, _ = ms.gen_integrals(norb, nocc, seed)
+    m = lib.MBE(0, keep_ci=1, precision=lib.MBE_MIXED_BF16X3)
+    m.load(h, eri, 2 * nocc)
+    res = m.run(ref, exp, 3, 0.0)
+    dh, dg = m.backward()
+    m.close()
+    odh, odg, _ = om.mbe_gradient(h, eri, nocc, ref, processed_tuples(res))
+    eh, eg = np.abs(dh - odh).max(), np.abs(dg - odg).max()
+    mh, mg = np.abs(odh).max(), np.abs(odg).max()
+    print(f"\n[parity] mixed-path backward: max |dE/dh - oracle| = {eh:.3e} "
+          f"({eh / mh:.2e} of the largest entry {mh:.2f}), max |dE/d(pq|rs) - oracle| = "
+          f"{eg:.3e} ({eg / mg:.2e} of {mg:.2f})")
+    assert eh < 2e-5 * mh and eg < 2e-5 * mg, (eh, eg, mh, mg)
