@@ -133,7 +133,7 @@ __device__ __forceinline__ int64_t gpair(int p, int q) {
 // One CTA per tuple.  act: n sorted global orbital ids.
 __global__ void k_effints(const double* __restrict__ h, const double* __restrict__ eri,
                           int norb, int nocc, int npair_g, const int32_t* __restrict__ act_all,
-                          int n, int nsig, double* ecore_out, double* heff_out, double* hp_out,
+                          int n, int nel, double* ecore_out, double* heff_out, double* hp_out,
                           double* gp_out, double* jk_out) {
   const int b = blockIdx.x;
   const int32_t* act = act_all + (int64_t)b * n;
@@ -199,9 +199,9 @@ __global__ void k_effints(const double* __restrict__ h, const double* __restrict
     hp_out[(int64_t)b * n * n + t] = s_hp[t];
   }
   __syncthreads();
-  // g'_{PQ} = (pq|rs) + (h'_pq d_rs + d_pq h'_rs) / N_active
+  // g'_{PQ} = (pq|rs) + (h'_pq d_rs + d_pq h'_rs) / N_active, N_active = nel
+  // active electrons of both spins (sum_r E_rr = N_active on the space)
   const int npair = n * (n + 1) / 2;
-  const int nel = 2 * nsig;
   const double inv = nel > 0 ? 1.0 / nel : 0.0;
   for (int t = threadIdx.x; t < npair * npair; t += blockDim.x) {
     int P = t / npair, Q = t % npair;
@@ -222,11 +222,11 @@ __global__ void k_effints(const double* __restrict__ h, const double* __restrict
 
 }  // namespace
 
-void launch_effints_raw(mbe_ctx* ctx, const int32_t* act, int B, int n, int nsig, double* ecore,
+void launch_effints_raw(mbe_ctx* ctx, const int32_t* act, int B, int n, int nel, double* ecore,
                         double* heff, double* hp, double* gp, double* jk) {
   size_t smem = 2 * sizeof(double) * n * n;
   k_effints<<<B, 256, smem, ctx->stream>>>(ctx->h.ptr, ctx->eri.ptr, ctx->norb, ctx->nocc,
-                                           ctx->npair_g, act, n, nsig, ecore, heff, hp, gp, jk);
+                                           ctx->npair_g, act, n, nel, ecore, heff, hp, gp, jk);
   CU_LAUNCH_CHECK();
 }
 
@@ -237,7 +237,8 @@ void launch_effints(mbe_ctx* ctx, BinProblem& bp) {
   bp.hp.reset(&ctx->pool, (size_t)B * n * n);
   bp.gp.reset(&ctx->pool, (size_t)B * bp.npair * bp.npair);
   bp.jk.reset(&ctx->pool, (size_t)B * 2 * n * n);
-  launch_effints_raw(ctx, bp.act.ptr, B, n, bp.nsig, bp.ecore.ptr, bp.heff.ptr, bp.hp.ptr,
+  const int nel = bp.nsig + (bp.nsigb < 0 ? bp.nsig : bp.nsigb);
+  launch_effints_raw(ctx, bp.act.ptr, B, n, nel, bp.ecore.ptr, bp.heff.ptr, bp.hp.ptr,
                      bp.gp.ptr, bp.jk.ptr);
 }
 

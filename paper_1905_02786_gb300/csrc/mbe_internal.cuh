@@ -254,6 +254,11 @@ struct mbe_ctx {
   bool kept_ref = false;
   KeptRdm ref_ci;
   std::vector<RdmBlock> rdm_blocks;
+  // autotuned operand plans of the two-spin tensor-core sigma:
+  // (n, nsig) -> (A stages, pull lists in shared memory); tune_file is the
+  // cache (empty: none)
+  std::map<std::pair<int, int>, std::pair<int, int>> tune_ab;
+  std::string tune_file;
   // warm-start vectors of the previous and the current order
   GuessStore guess_prev, guess_cur;
   // pi-pruning: partner[o] = the degenerate partner of expansion orbital o
@@ -319,7 +324,8 @@ void build_string_tables(mbe_ctx* ctx, StringTables* t);
 int64_t string_count(int n, int nsig);
 void launch_string_tables(mbe_ctx* ctx, int n, int nsig, int nstr, uint32_t* masks,
                           int32_t* link);
-void launch_effints_raw(mbe_ctx* ctx, const int32_t* act, int B, int n, int nsig, double* ecore,
+// nel: active electrons (both spins)
+void launch_effints_raw(mbe_ctx* ctx, const int32_t* act, int B, int n, int nel, double* ecore,
                         double* heff, double* hp, double* gp, double* jk);
 void sigma_fp64_raw(mbe_ctx* ctx, int n, int nsig, int nstr, const int32_t* link,
                     const uint32_t* masks, const double* gp, const double* c, int64_t c_stride,

@@ -123,7 +123,7 @@ int noalloc_sigma_run(mbe_ctx* ctx, const int* act, int nact, const double* c_de
   k_put_act<<<1, 32, 0, st>>>(al, nact, actd, bmap);
   CU_LAUNCH_CHECK();
   launch_string_tables(ctx, nact, nsig, (int)nstr, masks, link);
-  launch_effints_raw(ctx, actd, 1, nact, nsig, ecore, (double*)(base + L.heff),
+  launch_effints_raw(ctx, actd, 1, nact, 2 * nsig, ecore, (double*)(base + L.heff),
                      (double*)(base + L.hp), (double*)(base + L.gp), (double*)(base + L.jk));
   const int64_t ndet = nstr * nstr;
   sigma_fp64_raw(ctx, nact, nsig, (int)nstr, link, masks, (const double*)(base + L.gp), c_dev, ndet,

@@ -51,13 +51,19 @@ def merge_shards(parts, n: int, world: int, weights=None) -> np.ndarray:
     return out
 
 
-def tuple_weights(tuples: np.ndarray, ref, nocc: int) -> np.ndarray:
-    """Work estimate of each tuple's CASCI: its determinant count C(n, n_sigma)^2,
-    n = |Pi| + order active orbitals, n_sigma = occupied orbitals among them."""
+def tuple_weights(tuples: np.ndarray, ref, nocc) -> np.ndarray:
+    """Work estimate of each tuple's CASCI: its determinant count
+    C(n, n_alpha) C(n, n_beta), n = |Pi| + order active orbitals, n_alpha and
+    n_beta the occupied orbitals of each spin among them.  ``nocc``: an int
+    (closed shell) or (n_alpha, n_beta) occupied orbitals (high spin)."""
+    na, nb = (int(nocc[0]), int(nocc[1])) if isinstance(nocc, (tuple, list)) else (nocc, nocc)
     n = len(ref) + tuples.shape[1]
-    ns_ref = sum(1 for r in ref if r < nocc)
-    ns = ns_ref + (tuples < nocc).sum(axis=1)
-    return np.array([float(math.comb(n, int(s))) ** 2 for s in ns])
+    cnt = []
+    for occ in (na, nb):
+        base = sum(1 for r in ref if r < occ)
+        cnt.append(base + (tuples < occ).sum(axis=1))
+    return np.array([float(math.comb(n, int(a)) * math.comb(n, int(b)))
+                     for a, b in zip(*cnt)])
 
 
 def torch_allgather(group=None):
