@@ -266,6 +266,15 @@ def transfer_bytes(res, h, eri):
     return h2d, d2h
 
 
+def mbe_opts(args) -> dict:
+    """--mbe-opt name=value overrides of mbe_options fields (ints or floats)."""
+    out = {}
+    for item in args.mbe_opt or []:
+        k, v = item.split("=", 1)
+        out[k.strip()] = int(v) if v.strip().lstrip("-").isdigit() else float(v)
+    return out
+
+
 def run_profile_batch(args):
     """One mixed batch of seeded order-6 tuples of the 8e/23o workload (all
     with orbital 0: 8e/12o CASCIs, 245,025 determinants; or, with
@@ -279,7 +288,8 @@ def run_profile_batch(args):
     name = "h2o_dz_8e23o"
     w = ms.workload(name)
     h, eri, _ = ms.workload_integrals(name)
-    m = B.MBE(0, precision=B.MBE_MIXED_BF16X3, max_batch=4096, timing=1)
+    m = B.MBE(0, **{**dict(precision=B.MBE_MIXED_BF16X3, max_batch=4096, timing=1),
+                    **mbe_opts(args)})
     m.load(h, eri, w["nel"])
     B.mbe_set_reference(m.ctx, w["ref"], w["exp"])
     rest = [o for o in w["exp"] if o != 0]
@@ -292,12 +302,13 @@ def run_profile_batch(args):
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_push("solve")
     t0 = time.perf_counter()
-    B.mbe_solve_tuples(m.ctx, tuples, 6)
+    eps, _ = B.mbe_solve_tuples(m.ctx, tuples, 6)
     dt = time.perf_counter() - t0
     torch.cuda.nvtx.range_pop()
     st = B.mbe_get_stats(m.ctx)
     print(json.dumps({"profile_batch": n, "cas": "6e/12o" if args.profile_small else "8e/12o",
-                      "seconds": dt, "tuples_per_s": n / dt,
+                      "options": mbe_opts(args), "seconds": dt, "tuples_per_s": n / dt,
+                      "eps": [float(e) for e in eps],
                       "tc_tflops": st["dom_flops"] / st["dom_ms"] / 1e9 if st["dom_ms"] else None,
                       "stats": st}))
     m.close()
@@ -315,6 +326,8 @@ def main():
     ap.add_argument("--max-batch", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--mbe-opt", action="append", default=None, metavar="NAME=VALUE",
+                    help="override an mbe_options field (repeatable), e.g. max_subspace=12")
     ap.add_argument("--fd-check", type=int, default=0,
                     help="finite-difference check of the energy gradient on this many "
                          "seeded unique integrals of the differentiation workload")
@@ -354,9 +367,10 @@ def main():
     h, eri, _ = ms.workload_integrals(args.workload)
     max_order = args.max_order or w["max_order"]
     prec = B.MBE_MIXED_BF16X3 if args.precision == "mixed" else B.MBE_FP64
-    m = B.MBE(local, precision=prec, max_batch=args.max_batch, timing=1,
-              keep_ci=1 if args.backward else 0,
-              backward_share=(2 if rank == 0 else 1) if world > 1 else 0)
+    m = B.MBE(local, **{**dict(precision=prec, max_batch=args.max_batch, timing=1,
+                               keep_ci=1 if args.backward else 0,
+                               backward_share=(2 if rank == 0 else 1) if world > 1 else 0),
+                        **mbe_opts(args)})
     stream = torch.cuda.Stream()
     B.mbe_set_stream(m.ctx, stream.cuda_stream)
     m.load(h, eri, w["nel"])
@@ -556,7 +570,8 @@ def main():
                            "tuples_per_step": ntup // args.steps,
                            "l2": "256 MiB buffer written before each step (flushed); "
                                  "Davidson working set exceeds L2",
-                           "parallelism": f"tuple-sharded x{world}" if world > 1 else "1 GPU"},
+                           "parallelism": f"tuple-sharded x{world}" if world > 1 else "1 GPU",
+                           **({"options": mbe_opts(args)} if args.mbe_opt else {})},
                 "sigma_tflops": {
                     "tensor_core": (st["dom_flops"] / (st["dom_ms"] * 1e-3) / 1e12)
                     if st["dom_ms"] else None,

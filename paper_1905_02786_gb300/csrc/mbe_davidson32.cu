@@ -29,7 +29,6 @@
 
 namespace {
 
-constexpr int CH = 4096;     // elements per reduction chunk
 constexpr int RT = 256;      // threads of the reduction kernels
 
 __device__ __forceinline__ double block_sum(double v, double* red) {
@@ -43,27 +42,42 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;
 }
 
+// Every vector of the mixed Davidson iteration has L elements (N_det rounded
+// up to a multiple of 4, the padding kept at zero) and starts on a 16-byte
+// boundary, so the streaming kernels below move float4s.  A reduction chunk
+// is `ch` elements (a multiple of 1024, chosen per batch).
+
+__device__ __forceinline__ float dot4(const float4 a, const float4 b, float acc) {
+  acc = fmaf(a.x, b.x, acc);
+  acc = fmaf(a.y, b.y, acc);
+  acc = fmaf(a.z, b.z, acc);
+  return fmaf(a.w, b.w, acc);
+}
+
 // partial[b][i][chunk] = sum over the chunk of X[b][i][k] Y[b][k], i < m
-__global__ void k32_multidot(const float* __restrict__ X, int64_t xb, int64_t xv,
-                             const float* __restrict__ Y, int64_t yb, int m, int64_t N, int nchunks,
-                             const int32_t* __restrict__ active, double* __restrict__ partial) {
+__global__ void __launch_bounds__(RT) k32_multidot(const float* __restrict__ X, int64_t xb,
+                                                  int64_t xv, const float* __restrict__ Y,
+                                                  int64_t yb, int m, int64_t L, int ch,
+                                                  int nchunks, const int32_t* __restrict__ active,
+                                                  double* __restrict__ partial) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
   const int chunk = blockIdx.x;
-  const int64_t k0 = (int64_t)chunk * CH, k1 = min(N, k0 + CH);
+  const int64_t q0 = (int64_t)chunk * (ch >> 2), q1 = min(L >> 2, q0 + (ch >> 2));
   __shared__ double red[32][33];
-  const float* y = Y + (int64_t)b * yb;
+  const float4* y = reinterpret_cast<const float4*>(Y + (int64_t)b * yb);
   const float* x = X + (int64_t)b * xb;
   for (int i0 = 0; i0 < m; i0 += 16) {
     const int ni = min(16, m - i0);
     float acc[16];
 #pragma unroll
     for (int i = 0; i < 16; i++) acc[i] = 0.f;
-    for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
-      const float yv = y[k];
+    for (int64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+      const float4 yv = y[q];
 #pragma unroll
       for (int i = 0; i < 16; i++)
-        if (i < ni) acc[i] = fmaf(x[(int64_t)(i0 + i) * xv + k], yv, acc[i]);
+        if (i < ni)
+          acc[i] = dot4(reinterpret_cast<const float4*>(x + (int64_t)(i0 + i) * xv)[q], yv, acc[i]);
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -85,12 +99,12 @@ __global__ void k32_multidot(const float* __restrict__ X, int64_t xb, int64_t xv
 // error-free dot of two FP32 vectors: products split exactly (p + e = x y),
 // the p terms summed with compensation, all per-thread sums combined in FP64
 __global__ void k32_dot_comp(const float* __restrict__ X, int64_t xb, const float* __restrict__ Y,
-                             int64_t yb, int64_t N, int nchunks, const int32_t* __restrict__ active,
-                             double* __restrict__ partial) {
+                             int64_t yb, int64_t N, int ch, int nchunks,
+                             const int32_t* __restrict__ active, double* __restrict__ partial) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
   __shared__ double red[32];
-  const int64_t k0 = (int64_t)blockIdx.x * CH, k1 = min(N, k0 + CH);
+  const int64_t k0 = (int64_t)blockIdx.x * ch, k1 = min(N, k0 + ch);
   const float* x = X + (int64_t)b * xb;
   const float* y = Y + (int64_t)b * yb;
   // (s, lo): s + lo carries the running sum to ~2^-48 relative; every
@@ -178,7 +192,7 @@ __global__ void k32_converge(const double* __restrict__ partial, int nchunks, in
 // 32 x 32 tiles (I, J) and (J, I), I <= J, staged in shared memory so that
 // both the element and its transpose are read and written coalesced
 __global__ void k32_precondition(float* __restrict__ T, const float* __restrict__ hd, int nstr,
-                                 const double* __restrict__ theta,
+                                 int64_t ld, const double* __restrict__ theta,
                                  const int32_t* __restrict__ active) {
   const int b = blockIdx.y;
   if (!active[b]) return;
@@ -192,9 +206,8 @@ __global__ void k32_precondition(float* __restrict__ T, const float* __restrict_
   const int J = I + t;
   __shared__ float sT[2][32][33], sH[2][32][33];
   const float th = (float)theta[b];
-  const int64_t N = (int64_t)nstr * nstr;
-  float* Tb = T + (int64_t)b * N;
-  const float* hb = hd + (int64_t)b * N;
+  float* Tb = T + (int64_t)b * ld;
+  const float* hb = hd + (int64_t)b * ld;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
   for (int h = 0; h < 2; h++) {
     const int r0 = (h ? J : I) * 32, c0 = (h ? I : J) * 32;
@@ -222,7 +235,7 @@ __global__ void k32_precondition(float* __restrict__ T, const float* __restrict_
 }
 
 __global__ void k32_append(const float* __restrict__ T, float* __restrict__ V, int m, int M,
-                           int64_t N, const double* __restrict__ nrm2,
+                           int64_t L, const double* __restrict__ nrm2,
                            int32_t* __restrict__ active) {
   const int b = blockIdx.y;
   if (!active[b]) return;
@@ -236,9 +249,13 @@ __global__ void k32_append(const float* __restrict__ T, float* __restrict__ V, i
   if (threadIdx.x == 0) s_inv = (float)(1.0 / sqrt(n2));   // one FP64 root per block
   __syncthreads();
   const float inv = s_inv;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N;
-       k += (int64_t)gridDim.x * blockDim.x)
-    V[(int64_t)b * M * N + (int64_t)m * N + k] = T[(int64_t)b * N + k] * inv;
+  const float4* t4 = reinterpret_cast<const float4*>(T + (int64_t)b * L);
+  float4* v4 = reinterpret_cast<float4*>(V + (int64_t)b * M * L + (int64_t)m * L);
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (L >> 2);
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const float4 t = t4[q];
+    v4[q] = make_float4(t.x * inv, t.y * inv, t.z * inv, t.w * inv);
+  }
 }
 
 // Per-thread FP32 dot accumulators of the fused kernels below live in shared
@@ -297,10 +314,10 @@ __device__ __forceinline__ void sde_sums_to_partial(const float2 (*sDE)[RT], int
 // served by the caches, so V streams from HBM once instead of twice.
 __global__ void __launch_bounds__(RT) k32_residual_pre(
     const float* __restrict__ V, const float* __restrict__ AV, const float* __restrict__ RX,
-    int exact0, int m, int M, int64_t N, const double* __restrict__ y,
+    int exact0, int m, int M, int64_t L, const double* __restrict__ y,
     const double* __restrict__ theta, const double* __restrict__ thx,
     const float* __restrict__ hd, const int32_t* __restrict__ active, float* __restrict__ X,
-    float* __restrict__ T, int nchunks, double* __restrict__ rpart,
+    float* __restrict__ T, int ch, int nchunks, double* __restrict__ rpart,
     double* __restrict__ dpart, int olsen, float* __restrict__ Uo,
     double* __restrict__ upart, double* __restrict__ xpart) {
   const int b = blockIdx.y;
@@ -321,44 +338,71 @@ __global__ void __launch_bounds__(RT) k32_residual_pre(
   const float th = (float)theta[b];
   const float dth = exact0 ? (float)(thx[b] - theta[b]) : 0.f;
   const int i0 = exact0 ? 1 : 0;
-  const int64_t k0 = (int64_t)blockIdx.x * CH, k1 = min(N, k0 + CH);
-  const float* Vb = V + (int64_t)b * M * N;
-  const float* AVb = AV + (int64_t)b * M * N;
-  const float* hb = hd + (int64_t)b * N;
+  const int64_t Lq = L >> 2;
+  const int64_t q0 = (int64_t)blockIdx.x * (ch >> 2), q1 = min(Lq, q0 + (ch >> 2));
+  const float4* Vb = reinterpret_cast<const float4*>(V + (int64_t)b * M * L);
+  const float4* AVb = reinterpret_cast<const float4*>(AV + (int64_t)b * M * L);
+  const float4* hb = reinterpret_cast<const float4*>(hd + (int64_t)b * L);
+  const float4* RXb = reinterpret_cast<const float4*>(RX + (int64_t)b * L);
+  float4* Xb = reinterpret_cast<float4*>(X + (int64_t)b * L);
+  float4* Tb = reinterpret_cast<float4*>(T + (int64_t)b * L);
+  float4* Ub = olsen ? reinterpret_cast<float4*>(Uo + (int64_t)b * L) : nullptr;
   float acc = 0.f, xt = 0.f, xu = 0.f;
-  for (int64_t k = k0 + threadIdx.x; k < k1; k += RT) {
-    float x = 0.f, r = 0.f;
+  for (int64_t q = q0 + threadIdx.x; q < q1; q += RT) {
+    float xs[4] = {0.f, 0.f, 0.f, 0.f}, rs[4] = {0.f, 0.f, 0.f, 0.f};
     if (exact0) {
-      const float v0 = Vb[k];
-      x = sy[0] * v0;
-      r = sy[0] * (RX[(int64_t)b * N + k] + dth * v0);
+      const float4 v0 = Vb[q], rx = RXb[q];
+      const float v[4] = {v0.x, v0.y, v0.z, v0.w}, r0[4] = {rx.x, rx.y, rx.z, rx.w};
+#pragma unroll
+      for (int e = 0; e < 4; e++) {
+        xs[e] = sy[0] * v[e];
+        rs[e] = sy[0] * (r0[e] + dth * v[e]);
+      }
     }
+#pragma unroll 4
     for (int i = i0; i < m; i++) {
-      const float v = Vb[(int64_t)i * N + k];
-      x = fmaf(sy[i], v, x);
-      r = fmaf(sy[i], AVb[(int64_t)i * N + k] - th * v, r);
+      const float4 v4 = Vb[(int64_t)i * Lq + q], a4 = AVb[(int64_t)i * Lq + q];
+      const float v[4] = {v4.x, v4.y, v4.z, v4.w}, a[4] = {a4.x, a4.y, a4.z, a4.w};
+#pragma unroll
+      for (int e = 0; e < 4; e++) {
+        xs[e] = fmaf(sy[i], v[e], xs[e]);
+        rs[e] = fmaf(sy[i], a[e] - th * v[e], rs[e]);
+      }
     }
-    X[(int64_t)b * N + k] = x;
-    acc = fmaf(r, r, acc);
-    float d = th - hb[k];
-    if (fabsf(d) < 1e-4f) d = d < 0.f ? -1e-4f : 1e-4f;
-    const float t = r / d;
-    T[(int64_t)b * N + k] = t;
+    Xb[q] = make_float4(xs[0], xs[1], xs[2], xs[3]);
+    const float4 h4 = hb[q];
+    const float hv[4] = {h4.x, h4.y, h4.z, h4.w};
+    float ts[4], us[4];
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+      acc = fmaf(rs[e], rs[e], acc);
+      float d = th - hv[e];
+      if (fabsf(d) < 1e-4f) d = d < 0.f ? -1e-4f : 1e-4f;
+      ts[e] = rs[e] / d;
+      us[e] = xs[e] / d;
+    }
+    const float4 t = make_float4(ts[0], ts[1], ts[2], ts[3]);
+    Tb[q] = t;
     if (olsen) {
-      const float u = x / d;
-      Uo[(int64_t)b * N + k] = u;
-      xt = fmaf(x, t, xt);
-      xu = fmaf(x, u, xu);
+      const float4 u = make_float4(us[0], us[1], us[2], us[3]);
+      Ub[q] = u;
+#pragma unroll
+      for (int e = 0; e < 4; e++) {
+        xt = fmaf(xs[e], ts[e], xt);
+        xu = fmaf(xs[e], us[e], xu);
+      }
+#pragma unroll 4
       for (int i = 0; i < m; i++) {
-        const float v = Vb[(int64_t)i * N + k];
+        const float4 v = Vb[(int64_t)i * Lq + q];
         float2 a = sDE[i][threadIdx.x];
-        a.x = fmaf(v, t, a.x);
-        a.y = fmaf(v, u, a.y);
+        a.x = dot4(v, t, a.x);
+        a.y = dot4(v, u, a.y);
         sDE[i][threadIdx.x] = a;
       }
     } else {
+#pragma unroll 4
       for (int i = 0; i < m; i++)
-        sD[i][threadIdx.x] = fmaf(Vb[(int64_t)i * N + k], t, sD[i][threadIdx.x]);
+        sD[i][threadIdx.x] = dot4(Vb[(int64_t)i * Lq + q], t, sD[i][threadIdx.x]);
     }
   }
   const double tot = block_sum((double)acc, red);
@@ -414,9 +458,9 @@ __global__ void k32_sub_eps(float* __restrict__ T, const float* __restrict__ U,
 //   norm == 1: partials of T . T (the normalisation).
 __global__ void __launch_bounds__(RT) k32_orth_pass(float* __restrict__ T,
                                                    const float* __restrict__ V, int m, int M,
-                                                   int64_t N, const double* __restrict__ coef,
+                                                   int64_t L, const double* __restrict__ coef,
                                                    const int32_t* __restrict__ active, int norm,
-                                                   int nchunks, double* __restrict__ partial,
+                                                   int ch, int nchunks, double* __restrict__ partial,
                                                    const float* __restrict__ Uo,
                                                    const float* __restrict__ eps) {
   const int b = blockIdx.y;
@@ -428,24 +472,36 @@ __global__ void __launch_bounds__(RT) k32_orth_pass(float* __restrict__ T,
   if (!norm)
     for (int i = 0; i < m; i++) sD[i][threadIdx.x] = 0.f;
   __syncthreads();
-  const int64_t k0 = (int64_t)blockIdx.x * CH, k1 = min(N, k0 + CH);
-  const float* Vb = V + (int64_t)b * M * N;
-  float* Tb = T + (int64_t)b * N;
+  const int64_t Lq = L >> 2;
+  const int64_t q0 = (int64_t)blockIdx.x * (ch >> 2), q1 = min(Lq, q0 + (ch >> 2));
+  const float4* Vb = reinterpret_cast<const float4*>(V + (int64_t)b * M * L);
+  float4* Tb = reinterpret_cast<float4*>(T + (int64_t)b * L);
   float nacc = 0.f;
   // with Uo (first pass under Olsen's correction): T holds M^-1 r and the
   // update starts from t = M^-1 r - eps M^-1 x
   const float e = Uo ? eps[b] : 0.f;
-  const float* Ub = Uo ? Uo + (int64_t)b * N : nullptr;
-  for (int64_t k = k0 + threadIdx.x; k < k1; k += RT) {
-    float t = Tb[k];
-    if (Ub) t = fmaf(-e, Ub[k], t);
-    for (int i = 0; i < m; i++) t = fmaf(-sc[i], Vb[(int64_t)i * N + k], t);
-    Tb[k] = t;
+  const float4* Ub = Uo ? reinterpret_cast<const float4*>(Uo + (int64_t)b * L) : nullptr;
+  for (int64_t q = q0 + threadIdx.x; q < q1; q += RT) {
+    float4 t = Tb[q];
+    if (Ub) {
+      const float4 u = Ub[q];
+      t = make_float4(fmaf(-e, u.x, t.x), fmaf(-e, u.y, t.y), fmaf(-e, u.z, t.z),
+                      fmaf(-e, u.w, t.w));
+    }
+#pragma unroll 4
+    for (int i = 0; i < m; i++) {
+      const float4 v = Vb[(int64_t)i * Lq + q];
+      const float c = sc[i];
+      t = make_float4(fmaf(-c, v.x, t.x), fmaf(-c, v.y, t.y), fmaf(-c, v.z, t.z),
+                      fmaf(-c, v.w, t.w));
+    }
+    Tb[q] = t;
     if (norm) {
-      nacc = fmaf(t, t, nacc);
+      nacc = dot4(t, t, nacc);
     } else {
+#pragma unroll 4
       for (int i = 0; i < m; i++)
-        sD[i][threadIdx.x] = fmaf(Vb[(int64_t)i * N + k], t, sD[i][threadIdx.x]);
+        sD[i][threadIdx.x] = dot4(Vb[(int64_t)i * Lq + q], t, sD[i][threadIdx.x]);
     }
   }
   if (norm) {
@@ -585,9 +641,9 @@ __global__ void k32_string_energy(const uint32_t* __restrict__ masks, int nstr, 
   }
 }
 
-__global__ void k32_hdiag(const uint32_t* __restrict__ masks, int nstr, int n, int nsig,
-                          const double* __restrict__ jk_all, const float* __restrict__ estr,
-                          float shift, float* __restrict__ hd_all) {
+__global__ void k32_hdiag(const uint32_t* __restrict__ masks, int nstr, int64_t ld, int n,
+                          int nsig, const double* __restrict__ jk_all,
+                          const float* __restrict__ estr, float shift, float* __restrict__ hd_all) {
   const int b = blockIdx.y;
   __shared__ float sJ[MBE_MAX_ACT * MBE_MAX_ACT];
   for (int t = threadIdx.x; t < n * n; t += blockDim.x)
@@ -609,12 +665,13 @@ __global__ void k32_hdiag(const uint32_t* __restrict__ masks, int nstr, int n, i
         if (w) cross = fmaf((float)w, sJ[p * n + q], cross);
       }
     }
-    hd_all[(int64_t)b * N + i] =
+    hd_all[(int64_t)b * ld + i] =
         (eb[ia] + eb[ib]) + cross + shift * (float)(nsig - __popc(ma & mb));
   }
 }
 
-__global__ void k32_guess(const float* __restrict__ hd, int nstr, int M, float* __restrict__ V) {
+__global__ void k32_guess(const float* __restrict__ hd, int nstr, int64_t ld, int M,
+                          float* __restrict__ V) {
   const int b = blockIdx.x;
   const int64_t N = (int64_t)nstr * nstr;
   __shared__ float sv[256];
@@ -622,7 +679,7 @@ __global__ void k32_guess(const float* __restrict__ hd, int nstr, int M, float* 
   float best = 3.4e38f;
   int64_t bi = 0;
   for (int64_t k = threadIdx.x; k < N; k += blockDim.x) {
-    const float v = hd[(int64_t)b * N + k];
+    const float v = hd[(int64_t)b * ld + k];
     if (v < best) { best = v; bi = k; }
   }
   sv[threadIdx.x] = best;
@@ -639,8 +696,8 @@ __global__ void k32_guess(const float* __restrict__ hd, int nstr, int M, float* 
     }
     __syncthreads();
   }
-  float* Vb = V + (int64_t)b * M * N;
-  for (int64_t k = threadIdx.x; k < N; k += blockDim.x) Vb[k] = 0.f;
+  float* Vb = V + (int64_t)b * M * ld;
+  for (int64_t k = threadIdx.x; k < ld; k += blockDim.x) Vb[k] = 0.f;
   __syncthreads();
   if (threadIdx.x == 0) {
     const int64_t i0 = si[0];
@@ -673,12 +730,12 @@ __global__ void k32_exact_prep(const float* __restrict__ X, const double* __rest
 
 // partial sums of V0 . A V0 in FP64 (one FP64 FMA per element)
 __global__ void k32_exact_xax(const double* __restrict__ C64, const double* __restrict__ S64,
-                              int64_t N, int nchunks, const int32_t* __restrict__ active,
+                              int64_t N, int ch, int nchunks, const int32_t* __restrict__ active,
                               double* __restrict__ partial) {
   const int b = blockIdx.y;
   if (!active[b]) return;
   __shared__ double red[32];
-  const int64_t k0 = (int64_t)blockIdx.x * CH, k1 = min(N, k0 + CH);
+  const int64_t k0 = (int64_t)blockIdx.x * ch, k1 = min(N, k0 + ch);
   double acc = 0.0;
   for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x)
     acc = fma(C64[(int64_t)b * N + k], S64[(int64_t)b * N + k], acc);
@@ -688,14 +745,14 @@ __global__ void k32_exact_xax(const double* __restrict__ C64, const double* __re
 
 // r_x = A V0 - theta_x V0 (stored FP32) and partial sums of |r_x|^2
 __global__ void k32_exact_rx(const double* __restrict__ C64, const double* __restrict__ S64,
-                             const double* __restrict__ thx, int64_t N, int nchunks,
+                             const double* __restrict__ thx, int64_t N, int ch, int nchunks,
                              const int32_t* __restrict__ active, float* __restrict__ RX,
                              double* __restrict__ partial) {
   const int b = blockIdx.y;
   if (!active[b]) return;
   __shared__ double red[32];
   const double th = thx[b];
-  const int64_t k0 = (int64_t)blockIdx.x * CH, k1 = min(N, k0 + CH);
+  const int64_t k0 = (int64_t)blockIdx.x * ch, k1 = min(N, k0 + ch);
   double acc = 0.0;
   for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
     const double r = fma(-th, C64[(int64_t)b * N + k], S64[(int64_t)b * N + k]);
@@ -761,20 +818,41 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
                           double* x_out_dev, const GuessPlan* plan) {
   const int B = bp.B;
   const int M = std::max(4, std::min(32, ctx->opt.max_subspace));
-  const int64_t N = bp.ndet;
+  // N determinants per tuple; every vector takes L = N rounded up to a
+  // multiple of 4 elements (the padding stays zero: the sigma and diagonal
+  // kernels never write it, and every combination of zero elements is zero)
+  const int64_t N = bp.ndet, L = (N + 3) / 4 * 4;
   const double shift = ctx->opt.spin_shift;
   DevPool* P = &ctx->pool;
-  const int nchunks = (int)((N + CH - 1) / CH);
-  DevBuf<float> V(P, (size_t)B * M * N), AV(P, (size_t)B * M * N), hd(P, (size_t)B * N),
-      T(P, (size_t)B * N), X(P, (size_t)B * N), RX(P, (size_t)B * N);
-  DevBuf<double> C64(P, (size_t)B * N), S64(P, (size_t)B * N),
+  const int nsm = [&] {
+    int v = 0;
+    CU_CHECK(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, ctx->device));
+    return v;
+  }();
+  // reduction chunk: about four CTAs per SM over the batch, 1024..16384
+  // elements (a multiple of 1024)
+  int ch = 16384;
+  while (ch > 1024 && (int64_t)B * ((L + ch - 1) / ch) < 4 * (int64_t)nsm) ch >>= 1;
+  const int nchunks = (int)((L + ch - 1) / ch);
+  DevBuf<float> V(P, (size_t)B * M * L), AV(P, (size_t)B * M * L), hd(P, (size_t)B * L),
+      T(P, (size_t)B * L), X(P, (size_t)B * L), RX(P, (size_t)B * L);
+  DevBuf<double> C64(P, (size_t)B * L), S64(P, (size_t)B * L),
       G(P, (size_t)B * M * M), y(P, (size_t)B * M), yp(P, (size_t)B * M), theta(P, B),
       thx(P, B), rnorm(P, B), tolr(P, B), coef(P, (size_t)B * M), cdot(P, B), rdot(P, B),
       xx(P, B), xax(P, B), partial(P, (size_t)B * M * nchunks), rpart(P, (size_t)B * nchunks);
   DevBuf<int32_t> active(P, B), iters(P, B), nact(P, 1), mask(P, B);
   SigmaWork sw;
   cudaStream_t st = ctx->stream;
-  const int64_t eb = std::min<int64_t>((N + 255) / 256, 1024);
+  if (L != N) {
+    // zero padding (the vectors' tails are read by the streaming kernels)
+    CU_CHECK(cudaMemsetAsync(V.ptr, 0, sizeof(float) * B * M * L, st));
+    CU_CHECK(cudaMemsetAsync(AV.ptr, 0, sizeof(float) * B * M * L, st));
+    CU_CHECK(cudaMemsetAsync(hd.ptr, 0, sizeof(float) * B * L, st));
+    CU_CHECK(cudaMemsetAsync(RX.ptr, 0, sizeof(float) * B * L, st));
+    CU_CHECK(cudaMemsetAsync(C64.ptr, 0, sizeof(double) * B * L, st));
+    CU_CHECK(cudaMemsetAsync(S64.ptr, 0, sizeof(double) * B * L, st));
+  }
+  const int64_t eb = std::min<int64_t>((L + 255) / 256, 1024);
   const dim3 ge((unsigned)eb, B), gc(nchunks, B);
   const int ntl = (bp.nstr + 31) / 32;
   const dim3 gpre((unsigned)(ntl * (ntl + 1) / 2), B);
@@ -788,17 +866,17 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
     k32_string_energy<<<dim3((unsigned)((bp.nstr + 255) / 256), B), 256, 0, st>>>(
         bp.tab->masks.ptr, bp.nstr, bp.n, bp.heff.ptr, bp.jk.ptr, estr.ptr);
     CU_LAUNCH_CHECK();
-    k32_hdiag<<<ge, 256, 0, st>>>(bp.tab->masks.ptr, bp.nstr, bp.n, bp.nsig, bp.jk.ptr, estr.ptr,
-                                  (float)shift, hd.ptr);
+    k32_hdiag<<<ge, 256, 0, st>>>(bp.tab->masks.ptr, bp.nstr, L, bp.n, bp.nsig, bp.jk.ptr,
+                                  estr.ptr, (float)shift, hd.ptr);
     CU_LAUNCH_CHECK();
   }
   // P-space preconditioner: the lowest-diagonal block of A solved exactly,
   // with Olsen's correction (u = M^-1 x in U32, its dot partials in upart,
   // x.M^-1 r and x.M^-1 x in xpart)
   PspaceWork psp;
-  pspace_setup(ctx, bp, hd.ptr, shift, pspace_size(bp, ctx->opt.pspace), psp);
+  pspace_setup(ctx, bp, hd.ptr, L, shift, pspace_size(bp, ctx->opt.pspace), psp);
   const bool olsen = psp.npp > 0;
-  DevBuf<float> U32(P, olsen ? (size_t)B * N : 0), epsb(P, olsen ? (size_t)B : 0);
+  DevBuf<float> U32(P, olsen ? (size_t)B * L : 0), epsb(P, olsen ? (size_t)B : 0);
   DevBuf<double> upart(P, olsen ? (size_t)B * M * nchunks : 0),
       xpart(P, olsen ? (size_t)B * 2 * nchunks : 0), xsum(P, olsen ? (size_t)B * 2 : 0),
       coef2(P, olsen ? (size_t)B * M : 0);
@@ -810,9 +888,9 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
                                     2 * 32 * RT * (int)sizeof(float)));
     });
   }
-  k32_guess<<<B, 256, 0, st>>>(hd.ptr, bp.nstr, M, V.ptr);
+  k32_guess<<<B, 256, 0, st>>>(hd.ptr, bp.nstr, L, M, V.ptr);
   CU_LAUNCH_CHECK();
-  if (plan) launch_parent_guess(ctx, *plan, bp.n, bp.nsig, bp.nstr, V.ptr, nullptr, (int64_t)M * N);
+  if (plan) launch_parent_guess(ctx, *plan, bp.n, bp.nsig, bp.nstr, V.ptr, nullptr, (int64_t)M * L);
   k32_fill_i<<<1, 256, 0, st>>>(active.ptr, B, 1);
   CU_LAUNCH_CHECK();
   CU_CHECK(cudaMemsetAsync(iters.ptr, 0, sizeof(int32_t) * B, st));
@@ -822,7 +900,7 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
 
   auto dots = [&](const float* Xv, int64_t xb, int64_t xv, const float* Yv, int64_t yb, int m,
                   double* out, int64_t ob, int64_t oi, const int32_t* act) {
-    k32_multidot<<<dim3(nchunks, B), RT, 0, st>>>(Xv, xb, xv, Yv, yb, m, N, nchunks, act,
+    k32_multidot<<<dim3(nchunks, B), RT, 0, st>>>(Xv, xb, xv, Yv, yb, m, L, ch, nchunks, act,
                                                    partial.ptr);
     CU_LAUNCH_CHECK();
     k32_final<<<B, 32, 0, st>>>(partial.ptr, m, nchunks, act, out, ob, oi);
@@ -830,7 +908,8 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
   };
   auto dot_comp = [&](const float* Xv, int64_t xb, const float* Yv, int64_t yb, double* out,
                       const int32_t* act) {
-    k32_dot_comp<<<dim3(nchunks, B), RT, 0, st>>>(Xv, xb, Yv, yb, N, nchunks, act, partial.ptr);
+    k32_dot_comp<<<dim3(nchunks, B), RT, 0, st>>>(Xv, xb, Yv, yb, L, ch, nchunks, act,
+                                                   partial.ptr);
     CU_LAUNCH_CHECK();
     k32_final<<<B, 32, 0, st>>>(partial.ptr, 1, nchunks, act, out, 1, 1);
     CU_LAUNCH_CHECK();
@@ -857,13 +936,13 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
   // replaced first (the dot partials corrected with it).
   auto extend = [&](int m, bool raw, bool dots_ready) {
     if (raw) {
-      k32_precondition<<<gpre, 256, 0, st>>>(T.ptr, hd.ptr, bp.nstr, theta.ptr, active.ptr);
+      k32_precondition<<<gpre, 256, 0, st>>>(T.ptr, hd.ptr, bp.nstr, L, theta.ptr, active.ptr);
       CU_LAUNCH_CHECK();
     }
     // Olsen's combination goes with the P-space block (its exact block would
     // return t = -x); the exact-point residual (raw) takes the plain block
     const bool ols = olsen && !raw;
-    pspace_apply(ctx, bp, psp, T.ptr, hd.ptr, theta.ptr, V.ptr, m, M, nchunks, partial.ptr,
+    pspace_apply(ctx, bp, psp, T.ptr, hd.ptr, L, theta.ptr, V.ptr, m, M, nchunks, partial.ptr,
                  dots_ready, active.ptr, ols, U32.ptr, X.ptr, upart.ptr, xpart.ptr);
     if (ols) {
       k32_final<<<B, 32, 0, st>>>(xpart.ptr, 2, nchunks, active.ptr, xsum.ptr, 2, 1);
@@ -878,19 +957,19 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
                                   coef.ptr, epsb.ptr);
       CU_LAUNCH_CHECK();
       if (!dots_ready) {
-        k32_sub_eps<<<ge, 256, 0, st>>>(T.ptr, U32.ptr, epsb.ptr, N, active.ptr);
+        k32_sub_eps<<<ge, 256, 0, st>>>(T.ptr, U32.ptr, epsb.ptr, L, active.ptr);
         CU_LAUNCH_CHECK();
-        dots(V.ptr, (int64_t)M * N, N, T.ptr, N, m, coef.ptr, M, 1, active.ptr);
+        dots(V.ptr, (int64_t)M * L, L, T.ptr, L, m, coef.ptr, M, 1, active.ptr);
       }
     } else if (dots_ready) {
       k32_final<<<B, 32, 0, st>>>(partial.ptr, m, nchunks, active.ptr, coef.ptr, M, 1);
       CU_LAUNCH_CHECK();
     } else {
-      dots(V.ptr, (int64_t)M * N, N, T.ptr, N, m, coef.ptr, M, 1, active.ptr);
+      dots(V.ptr, (int64_t)M * L, L, T.ptr, L, m, coef.ptr, M, 1, active.ptr);
     }
     for (int pass = 0; pass < 2; pass++) {
       const bool fold = ols && dots_ready && pass == 0;   // t = t1 - eps u inside the pass
-      k32_orth_pass<<<gc, RT, 0, st>>>(T.ptr, V.ptr, m, M, N, coef.ptr, active.ptr, pass,
+      k32_orth_pass<<<gc, RT, 0, st>>>(T.ptr, V.ptr, m, M, L, coef.ptr, active.ptr, pass, ch,
                                       nchunks, partial.ptr, fold ? U32.ptr : nullptr,
                                       epsb.ptr);
       CU_LAUNCH_CHECK();
@@ -898,7 +977,7 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
                                   1);
       CU_LAUNCH_CHECK();
     }
-    k32_append<<<ge, 256, 0, st>>>(T.ptr, V.ptr, m, M, N, coef.ptr, active.ptr);
+    k32_append<<<ge, 256, 0, st>>>(T.ptr, V.ptr, m, M, L, coef.ptr, active.ptr);
     CU_LAUNCH_CHECK();
     k32_fix_frozen<<<1, 256, 0, st>>>(active.ptr, B);
     CU_LAUNCH_CHECK();
@@ -909,15 +988,15 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
   auto stage = [&](int m_start, int cap, int rel, bool exact0, int nact0) {
     int m = m_start, nact_h = nact0;
     for (int it = 0; it < cap && total_it < max_iter; it++, total_it++) {
-      sigma_tc(ctx, bp, sw, V.ptr + (int64_t)(m - 1) * N, (int64_t)M * N,
-               AV.ptr + (int64_t)(m - 1) * N, (int64_t)M * N, active.ptr, shift);
+      sigma_tc(ctx, bp, sw, V.ptr + (int64_t)(m - 1) * L, (int64_t)M * L,
+               AV.ptr + (int64_t)(m - 1) * L, (int64_t)M * L, active.ptr, shift);
       vecs_tc += nact_h;
-      dots(V.ptr, (int64_t)M * N, N, AV.ptr + (int64_t)(m - 1) * N, (int64_t)M * N, m, coef.ptr,
+      dots(V.ptr, (int64_t)M * L, L, AV.ptr + (int64_t)(m - 1) * L, (int64_t)M * L, m, coef.ptr,
            M, 1, active.ptr);
       if (exact0) {
-        dot_comp(V.ptr, (int64_t)M * N, V.ptr + (int64_t)(m - 1) * N, (int64_t)M * N, cdot.ptr,
+        dot_comp(V.ptr, (int64_t)M * L, V.ptr + (int64_t)(m - 1) * L, (int64_t)M * L, cdot.ptr,
                  active.ptr);
-        dots(RX.ptr, N, 0, V.ptr + (int64_t)(m - 1) * N, (int64_t)M * N, 1, rdot.ptr, 1, 1,
+        dots(RX.ptr, L, 0, V.ptr + (int64_t)(m - 1) * L, (int64_t)M * L, 1, rdot.ptr, 1, 1,
              active.ptr);
       }
       k32_store_row<<<B, 32, 0, st>>>(coef.ptr, cdot.ptr, rdot.ptr, thx.ptr, m, M, exact0 ? 1 : 0,
@@ -926,8 +1005,8 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
       k32_jacobi<<<B, 32, 0, st>>>(G.ptr, m, M, active.ptr, theta.ptr, y.ptr);
       CU_LAUNCH_CHECK();
       k32_residual_pre<<<gc, RT, (olsen ? 2 : 1) * m * RT * sizeof(float), st>>>(
-          V.ptr, AV.ptr, RX.ptr, exact0 ? 1 : 0, m, M, N, y.ptr, theta.ptr, thx.ptr, hd.ptr,
-          active.ptr, X.ptr, T.ptr, nchunks, rpart.ptr, partial.ptr, olsen ? 1 : 0, U32.ptr,
+          V.ptr, AV.ptr, RX.ptr, exact0 ? 1 : 0, m, M, L, y.ptr, theta.ptr, thx.ptr, hd.ptr,
+          active.ptr, X.ptr, T.ptr, ch, nchunks, rpart.ptr, partial.ptr, olsen ? 1 : 0, U32.ptr,
           upart.ptr, xpart.ptr);
       CU_LAUNCH_CHECK();
       k32_converge<<<1, 256, 0, st>>>(rpart.ptr, nchunks, B, m_start > 1 ? it + 1 : it, tolr.ptr,
@@ -940,7 +1019,7 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
       if (m == M) {
         k32_restart_coef<<<B, 32, 0, st>>>(y.ptr, yp.ptr, m, M, active.ptr, G.ptr);
         CU_LAUNCH_CHECK();
-        k32_restart_vec<<<ge, 256, 0, st>>>(V.ptr, AV.ptr, m, M, N, y.ptr, yp.ptr, active.ptr);
+        k32_restart_vec<<<ge, 256, 0, st>>>(V.ptr, AV.ptr, m, M, L, y.ptr, yp.ptr, active.ptr);
         CU_LAUNCH_CHECK();
         m = 2;
         restarted = 1;
@@ -959,18 +1038,18 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
   auto exact_point = [&]() {
     k32_copy_i<<<1, 256, 0, st>>>(mask.ptr, active.ptr, B);
     CU_LAUNCH_CHECK();
-    dot_comp(X.ptr, N, X.ptr, N, xx.ptr, active.ptr);
-    k32_exact_prep<<<ge, 256, 0, st>>>(X.ptr, xx.ptr, V.ptr, M, C64.ptr, N, active.ptr);
+    dot_comp(X.ptr, L, X.ptr, L, xx.ptr, active.ptr);
+    k32_exact_prep<<<ge, 256, 0, st>>>(X.ptr, xx.ptr, V.ptr, M, C64.ptr, L, active.ptr);
     CU_LAUNCH_CHECK();
-    dot_comp(V.ptr, (int64_t)M * N, V.ptr, (int64_t)M * N, xx.ptr, active.ptr);
+    dot_comp(V.ptr, (int64_t)M * L, V.ptr, (int64_t)M * L, xx.ptr, active.ptr);
     if (exact_fused) {
-      sigma_exact(ctx, bp, sw, V.ptr, (int64_t)M * N, S64.ptr, N, active.ptr);
-      launch_finish_sym_fp64(ctx, bp, S64.ptr, N, C64.ptr, N, shift, active.ptr);
+      sigma_exact(ctx, bp, sw, V.ptr, (int64_t)M * L, S64.ptr, L, active.ptr);
+      launch_finish_sym_fp64(ctx, bp, S64.ptr, L, C64.ptr, L, shift, active.ptr);
     } else {
-      sigma_fp64(ctx, bp, sw, C64.ptr, N, S64.ptr, N, active.ptr, shift, true, true);
+      sigma_fp64(ctx, bp, sw, C64.ptr, L, S64.ptr, L, active.ptr, shift, true, true);
     }
     vecs_ex += B;
-    k32_exact_xax<<<gc, RT, 0, st>>>(C64.ptr, S64.ptr, N, nchunks, active.ptr, rpart.ptr);
+    k32_exact_xax<<<gc, RT, 0, st>>>(C64.ptr, S64.ptr, L, ch, nchunks, active.ptr, rpart.ptr);
     CU_LAUNCH_CHECK();
     k32_final<<<B, 32, 0, st>>>(rpart.ptr, 1, nchunks, active.ptr, xax.ptr, 1, 1);
     CU_LAUNCH_CHECK();
@@ -979,7 +1058,7 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
                                                    active.ptr, thx.ptr, theta.ptr, G.ptr,
                                                    rnorm.ptr, iters.ptr);
     CU_LAUNCH_CHECK();
-    k32_exact_rx<<<gc, RT, 0, st>>>(C64.ptr, S64.ptr, thx.ptr, N, nchunks, active.ptr, RX.ptr,
+    k32_exact_rx<<<gc, RT, 0, st>>>(C64.ptr, S64.ptr, thx.ptr, L, ch, nchunks, active.ptr, RX.ptr,
                                     rpart.ptr);
     CU_LAUNCH_CHECK();
     k32_final<<<B, 32, 0, st>>>(rpart.ptr, 1, nchunks, active.ptr, rnorm.ptr, 1, 1);
@@ -1017,7 +1096,7 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
     k32_copy_i<<<1, 256, 0, st>>>(active.ptr, mask.ptr, B);
     CU_LAUNCH_CHECK();
     // the exact residual, preconditioned, is the first correction
-    CU_CHECK(cudaMemcpyAsync(T.ptr, RX.ptr, sizeof(float) * B * N, cudaMemcpyDeviceToDevice, st));
+    CU_CHECK(cudaMemcpyAsync(T.ptr, RX.ptr, sizeof(float) * B * L, cudaMemcpyDeviceToDevice, st));
     k32_save_yprev<<<B, 32, 0, st>>>(y.ptr, 1, M, 1, active.ptr, yp.ptr);
     CU_LAUNCH_CHECK();
     extend(1, true, false);
@@ -1026,7 +1105,7 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
   if (sigma_tc_error(ctx, sw)) throw MbeError{MBE_ETIMEOUT, "tensor-core sigma wait timed out"};
 
   // energies: E = E_core + theta_x - shift <S^2> (S^2 of the exact-point vector, FP64)
-  s2_apply(ctx, bp, C64.ptr, N, S64.ptr, N, nullptr);
+  s2_apply(ctx, bp, C64.ptr, L, S64.ptr, L, nullptr);
   std::vector<double> th(B), ec(B), rn(B), s2(B), nx(B);
   std::vector<int32_t> it_h(B);
   {
@@ -1034,11 +1113,11 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
     DevBuf<int32_t> all(P, B);
     k32_fill_i<<<1, 256, 0, st>>>(all.ptr, B, 1);
     CU_LAUNCH_CHECK();
-    k32_exact_xax<<<gc, RT, 0, st>>>(C64.ptr, S64.ptr, N, nchunks, all.ptr, rpart.ptr);
+    k32_exact_xax<<<gc, RT, 0, st>>>(C64.ptr, S64.ptr, L, ch, nchunks, all.ptr, rpart.ptr);
     CU_LAUNCH_CHECK();
     k32_final<<<B, 32, 0, st>>>(rpart.ptr, 1, nchunks, all.ptr, coef.ptr, 1, 1);
     CU_LAUNCH_CHECK();
-    k32_exact_xax<<<gc, RT, 0, st>>>(C64.ptr, C64.ptr, N, nchunks, all.ptr, rpart.ptr);
+    k32_exact_xax<<<gc, RT, 0, st>>>(C64.ptr, C64.ptr, L, ch, nchunks, all.ptr, rpart.ptr);
     CU_LAUNCH_CHECK();
     k32_final<<<B, 32, 0, st>>>(rpart.ptr, 1, nchunks, all.ptr, xax.ptr, 1, 1);
     CU_LAUNCH_CHECK();
@@ -1050,7 +1129,8 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
   CU_CHECK(cudaMemcpyAsync(nx.data(), xax.ptr, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
   CU_CHECK(cudaMemcpyAsync(it_h.data(), iters.ptr, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, st));
   if (x_out_dev)
-    CU_CHECK(cudaMemcpyAsync(x_out_dev, C64.ptr, sizeof(double) * B * N, cudaMemcpyDeviceToDevice, st));
+    CU_CHECK(cudaMemcpy2DAsync(x_out_dev, sizeof(double) * N, C64.ptr, sizeof(double) * L,
+                               sizeof(double) * N, B, cudaMemcpyDeviceToDevice, st));
   CU_CHECK(cudaStreamSynchronize(st));
 
   for (int b = 0; b < B; b++) {

@@ -308,12 +308,13 @@ struct PspaceWork {
 };
 // the P-space size used for a bin (0: off) given the requested size
 int pspace_size(const BinProblem& bp, int requested);
-void pspace_setup(mbe_ctx* ctx, BinProblem& bp, const float* hd, double shift, int npp,
-                  PspaceWork& w);
+// hd, T, V, Uo, X: one vector per tuple every ld elements
+void pspace_setup(mbe_ctx* ctx, BinProblem& bp, const float* hd, int64_t ld, double shift,
+                  int npp, PspaceWork& w);
 // the P-space block of t (and with olsen of u = M^-1 x in Uo, X the Ritz
 // vector), correcting the partial dot products that the residual kernel left
 void pspace_apply(mbe_ctx* ctx, const BinProblem& bp, const PspaceWork& w, float* T,
-                  const float* hd, const double* theta, const float* V, int m, int M,
+                  const float* hd, int64_t ld, const double* theta, const float* V, int m, int M,
                   int nchunks, double* partial, bool fix_dots, const int32_t* active,
                   bool olsen, float* Uo, const float* X, double* upart, double* xpart);
 

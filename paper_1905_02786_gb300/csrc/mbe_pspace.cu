@@ -70,11 +70,11 @@ __device__ __forceinline__ int block_flag_scan(bool f, int* s_warp, int* total) 
 // psel[b][0..npp) = linear indices a nstr + c (a <= c) of the npp canonical
 // pairs of lowest diagonal, in increasing index order
 __global__ void __launch_bounds__(SEL_THREADS)
-    k_psp_select(const float* __restrict__ hd_all, int nstr, int npp,
+    k_psp_select(const float* __restrict__ hd_all, int nstr, int64_t ld, int npp,
                  int32_t* __restrict__ psel) {
   const int b = blockIdx.x;
   const int64_t N = (int64_t)nstr * nstr;
-  const float* hd = hd_all + (int64_t)b * N;
+  const float* hd = hd_all + (int64_t)b * ld;
   __shared__ uint32_t hist[256];
   __shared__ uint32_t s_prefix;
   __shared__ int s_k;
@@ -214,8 +214,8 @@ __host__ __device__ inline EigShared eig_layout(int n) {
 __global__ void __launch_bounds__(EIG_THREADS)
     k_psp_eigh(const uint32_t* __restrict__ masks, int nstr, int n, int nsig,
                const double* __restrict__ heff_all, const double* __restrict__ hp_all,
-               const double* __restrict__ gp_all, const float* __restrict__ hd_all, float lam,
-               int npp, const int32_t* __restrict__ psel, float* __restrict__ lam_out,
+               const double* __restrict__ gp_all, const float* __restrict__ hd_all, int64_t ld,
+               float lam, int npp, const int32_t* __restrict__ psel, float* __restrict__ lam_out,
                float* __restrict__ U_out) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int b = blockIdx.x;
@@ -233,7 +233,6 @@ __global__ void __launch_bounds__(EIG_THREADS)
   __shared__ float s_red[32];
   __shared__ int s_done;
   const int tid = threadIdx.x;
-  const int64_t N = (int64_t)nstr * nstr;
   // (pq|rs) = g'_PQ - (h'_pq d_rs + d_pq h'_rs) / N_active (the definition of g')
   const double* gp = gp_all + (int64_t)b * npair * npair;
   const double* hp = hp_all + (int64_t)b * n * n;
@@ -259,7 +258,7 @@ __global__ void __launch_bounds__(EIG_THREADS)
     s_ma[u] = masks[a];
     s_mb[u] = masks[c];
     s_diag[u] = a == c;
-    s_hd[u] = hd_all[(int64_t)b * N + i];
+    s_hd[u] = hd_all[(int64_t)b * ld + i];
   }
   // an odd npp gets one decoupled pad index (zero row and column)
   const int m = (npp + 1) & ~1;
@@ -389,7 +388,7 @@ __global__ void __launch_bounds__(EIG_THREADS)
 // and the partial sums x.t, x.u (xpart) and, with fix_dots, V.u (upart)
 // take their changes.
 __global__ void __launch_bounds__(APPLY_THREADS)
-    k_psp_apply(float* __restrict__ T, const float* __restrict__ hd_all, int nstr,
+    k_psp_apply(float* __restrict__ T, const float* __restrict__ hd_all, int nstr, int64_t ld,
                 const double* __restrict__ theta, int npp, const int32_t* __restrict__ psel,
                 const float* __restrict__ U_all, const float* __restrict__ lam_all,
                 const float* __restrict__ V, int m, int M, int nchunks,
@@ -404,11 +403,10 @@ __global__ void __launch_bounds__(APPLY_THREADS)
   __shared__ float s_del[PSP_MAX], s_delu[PSP_MAX], s_xv[PSP_MAX];
   __shared__ int s_i[PSP_MAX];
   const int tid = threadIdx.x;
-  const int64_t N = (int64_t)nstr * nstr;
-  float* Tb = T + (int64_t)b * N;
-  float* Ob = olsen ? Uo + (int64_t)b * N : nullptr;
-  const float* Xb = olsen ? X + (int64_t)b * N : nullptr;
-  const float* hb = hd_all + (int64_t)b * N;
+  float* Tb = T + (int64_t)b * ld;
+  float* Ob = olsen ? Uo + (int64_t)b * ld : nullptr;
+  const float* Xb = olsen ? X + (int64_t)b * ld : nullptr;
+  const float* hb = hd_all + (int64_t)b * ld;
   const float th = (float)theta[b];
   const float* Ub = U_all + (int64_t)b * PSP_MAX * PSP_MAX;
   for (int t = tid; t < npp * npp; t += blockDim.x) {
@@ -485,11 +483,11 @@ __global__ void __launch_bounds__(APPLY_THREADS)
     }
   }
   if (!fix_dots) return;
-  const float* Vb = V + (int64_t)b * M * N;
+  const float* Vb = V + (int64_t)b * M * ld;
   for (int j = warp; j < m; j += APPLY_THREADS / 32) {
     double acc = 0.0, accu = 0.0;
     for (int u = lane; u < npp; u += 32) {
-      const double v = (double)Vb[(int64_t)j * N + s_i[u]];
+      const double v = (double)Vb[(int64_t)j * ld + s_i[u]];
       acc += v * (double)s_del[u];
       if (olsen) accu += v * (double)s_delu[u];
     }
@@ -515,8 +513,8 @@ int pspace_size(const BinProblem& bp, int requested) {
   return (int)cap;
 }
 
-void pspace_setup(mbe_ctx* ctx, BinProblem& bp, const float* hd, double shift, int npp,
-                  PspaceWork& w) {
+void pspace_setup(mbe_ctx* ctx, BinProblem& bp, const float* hd, int64_t ld, double shift,
+                  int npp, PspaceWork& w) {
   w.npp = npp;
   if (!npp) return;
   const int B = bp.B;
@@ -524,7 +522,7 @@ void pspace_setup(mbe_ctx* ctx, BinProblem& bp, const float* hd, double shift, i
   w.lam.reset(&ctx->pool, (size_t)B * PSP_MAX);
   w.U.reset(&ctx->pool, (size_t)B * PSP_MAX * PSP_MAX);
   cudaStream_t st = ctx->stream;
-  k_psp_select<<<B, SEL_THREADS, 0, st>>>(hd, bp.nstr, npp, w.sel.ptr);
+  k_psp_select<<<B, SEL_THREADS, 0, st>>>(hd, bp.nstr, ld, npp, w.sel.ptr);
   CU_LAUNCH_CHECK();
   const uint32_t smem = eig_layout(bp.n).total;
   static bool attr_set[MBE_MAX_DEVICES] = {false};
@@ -535,19 +533,19 @@ void pspace_setup(mbe_ctx* ctx, BinProblem& bp, const float* hd, double shift, i
                                   PSP_MAX * PSP_PITCH * 4));
   });
   k_psp_eigh<<<B, EIG_THREADS, smem, st>>>(bp.tab->masks.ptr, bp.nstr, bp.n, bp.nsig,
-                                           bp.heff.ptr, bp.hp.ptr, bp.gp.ptr, hd, (float)shift,
-                                           npp, w.sel.ptr, w.lam.ptr, w.U.ptr);
+                                           bp.heff.ptr, bp.hp.ptr, bp.gp.ptr, hd, ld,
+                                           (float)shift, npp, w.sel.ptr, w.lam.ptr, w.U.ptr);
   CU_LAUNCH_CHECK();
 }
 
 void pspace_apply(mbe_ctx* ctx, const BinProblem& bp, const PspaceWork& w, float* T,
-                  const float* hd, const double* theta, const float* V, int m, int M,
+                  const float* hd, int64_t ld, const double* theta, const float* V, int m, int M,
                   int nchunks, double* partial, bool fix_dots, const int32_t* active,
                   bool olsen, float* Uo, const float* X, double* upart, double* xpart) {
   if (!w.npp) return;
   const uint32_t smem = (uint32_t)w.npp * PSP_PITCH * 4;
   k_psp_apply<<<bp.B, APPLY_THREADS, smem, ctx->stream>>>(
-      T, hd, bp.nstr, theta, w.npp, w.sel.ptr, w.U.ptr, w.lam.ptr, V, m, M, nchunks, partial,
+      T, hd, bp.nstr, ld, theta, w.npp, w.sel.ptr, w.U.ptr, w.lam.ptr, V, m, M, nchunks, partial,
       fix_dots ? 1 : 0, active, olsen ? 1 : 0, Uo, X, upart, xpart);
   CU_LAUNCH_CHECK();
 }
