@@ -134,6 +134,19 @@ typedef struct mbe_options {
                               a poll lasts at most about a microsecond;
                               default 2^24 (seconds); 0 gives up at the first
                               wait (for tests of the error path)             */
+  int autotune;            /* 1: the first sigma call of each bin shape
+                              (n, n_sigma) of the mixed mode times every
+                              operand plan of the two-spin tensor-core kernel
+                              that fits (A-operand stages 2..4, pull lists in
+                              shared or global memory) on its own data and
+                              keeps the fastest for the shape; 0 (default):
+                              the most stages that fit, lists in shared
+                              memory when they fit.  All plans give the same
+                              bits.                                          */
+  const char* tune_file;   /* autotune cache (may be NULL): read at
+                              mbe_create, one line per tuned shape appended
+                              as it is tuned ("sigma_ab n nsig nstages
+                              pull_smem ms"); the string is copied           */
 } mbe_options;
 
 typedef struct mbe_ctx mbe_ctx;

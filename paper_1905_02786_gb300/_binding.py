@@ -45,7 +45,8 @@ class mbe_options(ctypes.Structure):
                 ("backward_share", ctypes.c_int), ("warm_start", ctypes.c_int),
                 ("mixed_stage_tol", ctypes.c_double), ("mixed_round_drop", ctypes.c_double),
                 ("mixed_rel_tol", ctypes.c_double), ("pspace", ctypes.c_int),
-                ("wait_limit", ctypes.c_int64)]
+                ("wait_limit", ctypes.c_int64), ("autotune", ctypes.c_int),
+                ("tune_file", ctypes.c_char_p)]
 
 
 _lib = None

@@ -2,6 +2,8 @@
 // space, batched CASCI solves, increments, tuple generation, gradient.
 #include "mbe_internal.cuh"
 #include <tuple>
+#include <fstream>
+#include <sstream>
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -317,6 +319,8 @@ void mbe_default_options(mbe_options* o) {
   o->mixed_rel_tol = 2e-7;
   o->pspace = 128;
   o->wait_limit = 1LL << 24;
+  o->autotune = 0;
+  o->tune_file = nullptr;
 }
 
 int mbe_create(mbe_ctx** out, int device, const mbe_options* opt) {
@@ -331,7 +335,8 @@ int mbe_create(mbe_ctx** out, int device, const mbe_options* opt) {
   if (o.max_batch < 1 || o.max_subspace < 4 || o.max_subspace > 32 || o.max_iter < 1)
     return MBE_EINVAL;
   if (!(o.mixed_stage_tol > 0.0) || !(o.mixed_round_drop > 0.0 && o.mixed_round_drop < 1.0) ||
-      !(o.mixed_rel_tol > 0.0) || o.pspace < 0 || o.pspace > 128 || o.wait_limit < 0)
+      !(o.mixed_rel_tol > 0.0) || o.pspace < 0 || o.pspace > 128 || o.wait_limit < 0 ||
+      (o.autotune != 0 && o.autotune != 1))
     return MBE_EINVAL;
   int ndev = 0;
   if (device < 0 || device >= MBE_MAX_DEVICES) return MBE_EINVAL;
@@ -343,6 +348,21 @@ int mbe_create(mbe_ctx** out, int device, const mbe_options* opt) {
   mbe_ctx* c = new mbe_ctx();
   c->device = device;
   c->opt = o;
+  c->opt.tune_file = nullptr;   // the caller's string is not kept
+  if (o.tune_file) {
+    c->tune_file = o.tune_file;
+    // cached plans: "sigma_ab n nsig nstages pull_smem ms" per line
+    std::ifstream in(c->tune_file);
+    std::string line;
+    while (std::getline(in, line)) {
+      std::istringstream ls(line);
+      std::string tag;
+      int n = 0, ns = 0, nst = 0, ps = 0;
+      if (ls >> tag >> n >> ns >> nst >> ps && tag == "sigma_ab" && nst >= 2 && nst <= 4 &&
+          (ps == 0 || ps == 1))
+        c->tune_ab[{n, ns}] = {nst, ps};
+    }
+  }
   c->pool.cap = o.mem_cap_bytes;
   if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
     delete c;

@@ -37,6 +37,7 @@
 #include "mbe_tcgen05.cuh"
 #include <cuda_bf16.h>
 #include <algorithm>
+#include <fstream>
 
 namespace {
 
@@ -815,6 +816,16 @@ inline bool ab_plan(int n, int nsig, int nstr, AbPlan& p) {
   return false;
 }
 
+// a given operand plan (nst A stages, pull lists in shared memory or not),
+// if its layout fits
+inline bool ab_plan_with(int n, int nsig, int nstr, int nst, int ps, AbPlan& p) {
+  if (!ab_plan(n, nsig, nstr, p)) return false;
+  if (nst < 2 || nst > AB_MAX_STAGES) return false;
+  p.nst = nst;
+  p.L = ab_layout(p.kp, p.kl, p.nst, nstr, p.nlink, ps);
+  return p.L.total <= AB_SMEM_MAX && p.L.pull_smem == (ps != 0);
+}
+
 template <int KP, bool PS>
 void launch_ab_kps(int device, int grid, const AbPlan& p, cudaStream_t st, const int32_t* lnk,
                    const int16_t* plist, const int32_t* poff, int nstr, const bf16* gh,
@@ -895,6 +906,16 @@ void sigma_tc(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const float* c, int64_
   AbPlan p;
   if (!ab_plan(bp.n, bp.nsig, nstr, p))
     throw MbeError{MBE_EINVAL, "active space too large for the tensor-core sigma"};
+  // autotuned plan of this shape, if one is known
+  bool tune_now = false;
+  if (ctx->opt.autotune && p.nlink > 0) {
+    auto it = ctx->tune_ab.find({bp.n, bp.nsig});
+    AbPlan q;
+    if (it == ctx->tune_ab.end())
+      tune_now = true;
+    else if (ab_plan_with(bp.n, bp.nsig, nstr, it->second.first, it->second.second, q))
+      p = q;
+  }
   const int64_t N = bp.ndet;
   const int64_t hs = 2 * (int64_t)nstr * p.ldc;      // bf16 elements per tuple (hi + lo)
   const int ntiles = (nstr + AB_M - 1) / AB_M;
@@ -947,6 +968,59 @@ void sigma_tc(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const float* c, int64_
     CU_LAUNCH_CHECK();
   }
   const long long wl = ctx->opt.wait_limit;
+  const int nt_g = (nstr + GM_T - 1) / GM_T;
+  const int grid_ab = (int)std::min<int64_t>((int64_t)B * nstr, nsm);
+  if (tune_now) {
+    // every plan that fits, timed on this call's data (H^a c rewritten
+    // before each, so W ends correct whichever runs last); the best of two
+    // timed launches per plan counts
+    static bool attr_done[MBE_MAX_DEVICES] = {false};
+    once_per_device(attr_done, ctx->device, [] {
+      CU_CHECK(cudaFuncSetAttribute(k_gemm_haa, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)G_SMEM));
+    });
+    cudaEvent_t e0, e1;
+    CU_CHECK(cudaEventCreate(&e0));
+    CU_CHECK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_nst = p.nst, best_ps = p.L.pull_smem ? 1 : 0;
+    for (int nst = 2; nst <= AB_MAX_STAGES; nst++)
+      for (int ps = 0; ps <= 1; ps++) {
+        AbPlan q;
+        if (!ab_plan_with(bp.n, bp.nsig, nstr, nst, ps, q)) continue;
+        float t = 1e30f;
+        for (int rep = 0; rep < 3; rep++) {
+          k_gemm_haa<<<dim3(nt_g * nt_g, B), G_THREADS, G_SMEM, st>>>(
+              (const bf16*)bp.haa.ptr, cs, hs, nstr, p.ldc, active, w.Xf.ptr, N, wl, w.err.ptr);
+          CU_LAUNCH_CHECK();
+          CU_CHECK(cudaEventRecord(e0, st));
+          launch_ab(ctx->device, grid_ab, q, st, tab->lnk.ptr, tab->plist.ptr, tab->poff.ptr,
+                    nstr, (const bf16*)bp.gsplit.ptr, cs, hs, active, B, w.Xf.ptr, N, wl,
+                    w.err.ptr);
+          CU_LAUNCH_CHECK();
+          CU_CHECK(cudaEventRecord(e1, st));
+          CU_CHECK(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          CU_CHECK(cudaEventElapsedTime(&ms, e0, e1));
+          if (rep > 0) t = std::min(t, ms);
+        }
+        if (t < best) {
+          best = t;
+          best_nst = nst;
+          best_ps = ps;
+        }
+      }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->tune_ab[{bp.n, bp.nsig}] = {best_nst, best_ps};
+    AbPlan q;
+    if (ab_plan_with(bp.n, bp.nsig, nstr, best_nst, best_ps, q)) p = q;
+    if (!ctx->tune_file.empty()) {
+      std::ofstream out(ctx->tune_file, std::ios::app);
+      out << "sigma_ab " << bp.n << " " << bp.nsig << " " << best_nst << " " << best_ps << " "
+          << best << "\n";
+    }
+  }
   cudaEvent_t ev;
   ctx->dom_timer.begin(st, ctx->opt.timing != 0, &ev);
   {
@@ -955,15 +1029,12 @@ void sigma_tc(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const float* c, int64_
       CU_CHECK(cudaFuncSetAttribute(k_gemm_haa, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)G_SMEM));
     });
-    const int nt = (nstr + GM_T - 1) / GM_T;
-    k_gemm_haa<<<dim3(nt * nt, B), G_THREADS, G_SMEM, st>>>((const bf16*)bp.haa.ptr, cs, hs, nstr,
-                                                            p.ldc, active, w.Xf.ptr, N, wl,
-                                                            w.err.ptr);
+    k_gemm_haa<<<dim3(nt_g * nt_g, B), G_THREADS, G_SMEM, st>>>(
+        (const bf16*)bp.haa.ptr, cs, hs, nstr, p.ldc, active, w.Xf.ptr, N, wl, w.err.ptr);
     CU_LAUNCH_CHECK();
   }
   if (p.nlink > 0) {
-    const int grid = (int)std::min<int64_t>((int64_t)B * nstr, nsm);
-    launch_ab(ctx->device, grid, p, st, tab->lnk.ptr, tab->plist.ptr, tab->poff.ptr, nstr,
+    launch_ab(ctx->device, grid_ab, p, st, tab->lnk.ptr, tab->plist.ptr, tab->poff.ptr, nstr,
               (const bf16*)bp.gsplit.ptr, cs, hs, active, B, w.Xf.ptr, N, wl, w.err.ptr);
     CU_LAUNCH_CHECK();
   }
