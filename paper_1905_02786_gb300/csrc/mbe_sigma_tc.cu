@@ -12,14 +12,16 @@
 //   sigma = H^a c + c H^a + Z,   H^a = 1/2 sum_PQ g'_PQ L_P L_Q,
 //   Z = sum_PQ g'_PQ L_P c L_Q,
 // H^a is symmetric, and Z is symmetric for symmetric c.  Here
-//   W = H^a c + Z/2,   sigma = W + W^T + shift S^2 c   (bitwise symmetric)
+//   W = H^a c + Z_u,   sigma = W + W^T + shift S^2 c   (bitwise symmetric)
+// with Z_u the upper triangle of Z (a < J) and half its diagonal, so that
+// the scatter of Z runs over half the strings
 // computed by
 //   k_build_haa  H^a row by row from the link table (FP64), split into bf16
 //                hi/lo rows, once per batch;
 //   k_split_c    c into bf16 hi/lo rows, once per call;
 //   k_gemm_haa   W = H^a c, a dense N_str^3 GEMM (c^T = c gives the B
 //                operand as rows of c);
-//   k_sigma_ab   W += Z/2: Z/2 = sum_Q F_Q L_Q with
+//   k_sigma_ab   W += Z_u from Z/2 = sum_Q F_Q L_Q with
 //                  F_Q(a, :) = sum_{P in links(a)} (g'_QP / 2) s_a(P) c(J_a(P), :)
 //                for one string a.  The MMA operand "rows J_a(P) of c" is a
 //                plain copy of rows (MN-major, cp.async), the other operand
@@ -27,7 +29,7 @@
 //                n_link pairs that link a, the same count for every string);
 //                the product for 128 column strings lands in TMEM and the
 //                scatter through the link table of the column strings adds
-//                it into row a of W in shared memory;
+//                it into row a of W (columns J >= a) in shared memory;
 //   k_sigma_tc_finish  sigma = W + W^T + shift S^2 c.
 // Both products run as split-BF16x3 (hi*hi + lo*hi + hi*lo, FP32
 // accumulation in TMEM): ~16 significant bits per operand, sigma to ~1e-4 of
@@ -688,8 +690,9 @@ k_sigma_ab(const int32_t* __restrict__ lnk, const int16_t* __restrict__ plist,
         __syncwarp();
         if (lane == 0) mbar_arrive(&acc_empty[sb]);
         bar_sync_n(1, AB_EPI_THREADS);
-        // pull: W(a, J) += sum over the links of J into this tile
-        for (int J = et; J < nstr; J += AB_EPI_THREADS) {
+        // pull: W(a, J) += sum over the links of J into this tile, for J >= a
+        // only (Z is symmetric: the lower triangle comes from the transpose)
+        for (int J = a + et; J < nstr; J += AB_EPI_THREADS) {
           const int32_t* po = PO + J * (ntiles + 1) + t;
           const int lo = po[0], hi = po[1];
           const int16_t* pl = PL + J * nlink;
@@ -718,8 +721,11 @@ k_sigma_ab(const int32_t* __restrict__ lnk, const int16_t* __restrict__ plist,
         }
       }
       if (!ok) break;
+      // F carries g'/2: the upper triangle takes Z(a, J) = 2 (F pulled), the
+      // diagonal Z(a, a) / 2, so that sigma = W + W^T holds Z once
       float* wr = W + (int64_t)b * w_stride + (int64_t)a * nstr;
-      for (int J = et; J < nstr; J += AB_EPI_THREADS) wr[J] += sAcc[J];
+      for (int J = a + et; J < nstr; J += AB_EPI_THREADS)
+        wr[J] += J > a ? 2.f * sAcc[J] : sAcc[J];
     }
     if (!ok && et == 0) {
       *abort_v = 1;
