@@ -36,12 +36,16 @@ def allorder(name):
     print(name, "done in", time.time() - t0, "s; total", res["total"])
 
 
-# seeded tuples of the high orders, whose CASCIs are too large for the
-# oracle's Davidson in test time: (order, count, seed, with orbital 0).
-# With occupied orbital 0 in the tuple the CASCI has 8 electrons, else 6.
+# seeded tuples whose CASCIs are too large for the oracle's Davidson in test
+# time: (order, count, seed, with orbital 0).  For the 8e/23o workload, with
+# occupied orbital 0 in the tuple the CASCI has 8 electrons, else 6; None
+# samples the whole expansion space (the 10e/60o and 8e/114o workloads, whose
+# expansion spaces hold virtual orbitals only).
 SAMPLES = {
     "h2o_dz_8e23o_sampled": ("h2o_dz_8e23o", [(5, 2, 61, True), (5, 1, 62, False),
                                               (6, 2, 63, True), (6, 2, 64, False)]),
+    "h10_chain_10e60o_sampled": ("h10_chain_10e60o", [(1, 2, 71, None), (2, 1, 72, None)]),
+    "h2o_qz_8e114o_sampled": ("h2o_qz_8e114o", [(1, 3, 73, None), (2, 3, 74, None)]),
 }
 
 
@@ -49,6 +53,10 @@ def sample_tuples(w, spec):
     rest = [o for o in w["exp"] if o != 0]
     out = []
     for order, count, seed, with0 in spec:
+        if with0 is None:
+            for t in ms.sample_tuples(w["exp"], order, count, seed):
+                out.append((order, tuple(sorted(t))))
+            continue
         for t in ms.sample_tuples(rest, order - 1 if with0 else order, count, seed):
             out.append((order, tuple(sorted(((0,) if with0 else ()) + t))))
     return out

@@ -13,6 +13,9 @@
   dominate the benchmark) in the mixed mode against stored oracle energies
   (tests/golden/h2o_dz_8e23o_sampled.txt, written by make_golden.py from
   oracle/ alone), to 1e-8 Eh.
+* CASCI energies of seeded order-1 and order-2 tuples of the 10e/60o chain
+  and the 8e/114o workload (stored oracle energies), mixed 1e-8 Eh, FP64
+  1e-10 Eh.
 * The all-order 8e/12o expansion (255 tuples) in the mixed mode against the
   stored oracle energies: 1e-8 Eh per CASCI energy, 1e-7 Eh per increment
   (the mixed-precision target of Eq. 3's increments), and the total against
@@ -152,6 +155,35 @@ def test_mixed_energies_order5_order6_vs_oracle(lib):
     m.close()
     print(f"\n[parity] mixed CASCI energies, orders 5-6 of 8e/23o: max |E - E_oracle| = {worst:.3e} Eh")
     assert nel == {(5, True), (5, False), (6, True), (6, False)}
+
+
+@pytest.mark.parametrize("name", ["h10_chain_10e60o", "h2o_qz_8e114o"])
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_large_workload_energies_vs_oracle(lib, name, precision):
+    """Seeded order-1 and order-2 tuples of the 10e/60o chain (10e/11o and
+    10e/12o CASCIs, 213,444 and 627,264 determinants) and of the 8e/114o
+    production-size workload (8e/9o and 8e/10o) against stored oracle
+    energies: 1e-8 Eh in the mixed mode, 1e-10 Eh in FP64."""
+    w = ms.workload(name)
+    h, eri, _ = ms.workload_integrals(name)
+    gold = _sampled_golden(name + "_sampled")
+    prec = lib.MBE_MIXED_BF16X3 if precision == "mixed" else lib.MBE_FP64
+    tol = 1e-8 if precision == "mixed" else 1e-10
+    m = lib.MBE(0, precision=prec)
+    m.load(h, eri, w["nel"])
+    e_ref = lib.mbe_set_reference(m.ctx, w["ref"], w["exp"])
+    assert abs(e_ref - gold[0][0][1]) < tol
+    worst = 0.0
+    for order in sorted(k for k in gold if k > 0):
+        tuples = [t for t, _ in gold[order]]
+        eps, st = lib.mbe_solve_tuples(m.ctx, np.array(tuples, dtype=np.int32), order)
+        assert np.all(st == 0)
+        for (t, e_or), e in zip(gold[order], eps):
+            assert abs(e - e_or) < tol, (order, t, e, e_or)
+            worst = max(worst, abs(e - e_or))
+    m.close()
+    print(f"\n[parity] {precision} CASCI energies of {name} (orders 1-2): "
+          f"max |E - E_oracle| = {worst:.3e} Eh")
 
 
 def test_allorder_fci8e12o_mixed_matches_golden(lib):
