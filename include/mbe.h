@@ -80,7 +80,10 @@ typedef struct mbe_options {
   int precision;        /* MBE_FP64 or MBE_MIXED_BF16X3                      */
   int max_batch;        /* max tuples solved together in one bin (>= 1); 1
                            gives the one-tuple-at-a-time path               */
-  int max_subspace;     /* Davidson subspace size before restart (4..32)     */
+  int max_subspace;     /* Davidson subspace size before restart (4..32); in
+                           the mixed mode a refinement round that fills its
+                           subspace makes the later rounds of the batch use
+                           up to 12 more vectors (at most 32)               */
   int max_iter;         /* Davidson iteration cap per tuple                  */
   double conv_tol_r;    /* residual-norm tolerance of the Davidson iteration */
   double conv_tol_e;    /* energy-change tolerance                           */

@@ -196,7 +196,8 @@ void solve_jobs(mbe_ctx* ctx, const std::vector<std::vector<int>>& acts, double*
     // the mixed path works on alpha<->beta symmetric vectors: closed shells
     const bool mixed_bin = ctx->opt.precision == MBE_MIXED_BF16X3 && N > 1 && closed &&
                            sigma_tc_supported(n, tab->nstr) && ozaki_supported(tab->npair);
-    double per = (mixed_bin ? (double)(8 * M + 46) * N + 128.0 * 129.0 * 4.0
+    const int Mm = mixed_subspace_alloc(ctx->opt.max_subspace);
+    double per = (mixed_bin ? (double)(8 * Mm + 46) * N + 128.0 * 129.0 * 4.0
                             : (double)(2 * M + 6) * N * 8.0) +
                  (double)tab->npair * tab->npair * 8.0 * 2.0;
     int64_t bmem = std::max<int64_t>(1, (int64_t)(budget / per));

@@ -817,7 +817,11 @@ __global__ void k32_copy_i(const int32_t* s, int32_t* d, int n) {
 void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int32_t* status_host,
                           double* x_out_dev, const GuessPlan* plan) {
   const int B = bp.B;
-  const int M = std::max(4, std::min(32, ctx->opt.max_subspace));
+  // Ms: the subspace cap of the first stage and of a refinement round; M: the
+  // allocated size (stride), the cap of the rounds after one that ended with
+  // its subspace full and tuples still above their targets
+  const int Ms = std::max(4, std::min(32, ctx->opt.max_subspace));
+  const int M = mixed_subspace_alloc(ctx->opt.max_subspace);
   // N determinants per tuple; every vector takes L = N rounded up to a
   // multiple of 4 elements (the padding stays zero: the sigma and diagonal
   // kernels never write it, and every combination of zero elements is zero)
@@ -985,7 +989,9 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
   // Davidson iterations from a subspace of m_start vectors, the newest one's
   // sigma pending; exact0: V_0 is an exact point (no restart: the stage ends
   // when the subspace is full)
-  auto stage = [&](int m_start, int cap, int rel, bool exact0, int nact0) {
+  // returns true when an exact0 stage ended because its subspace (mcap
+  // vectors) was full with tuples still iterating
+  auto stage = [&](int m_start, int cap, int rel, bool exact0, int nact0, int mcap) -> bool {
     int m = m_start, nact_h = nact0;
     for (int it = 0; it < cap && total_it < max_iter; it++, total_it++) {
       sigma_tc(ctx, bp, sw, V.ptr + (int64_t)(m - 1) * L, (int64_t)M * L,
@@ -1013,10 +1019,10 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
                                       rel, theta.ptr, rnorm.ptr, active.ptr, iters.ptr, nact.ptr);
       CU_LAUNCH_CHECK();
       nact_h = count_active();
-      if (nact_h == 0) return;
-      if (exact0 && m == M) return;
+      if (nact_h == 0) return false;
+      if (exact0 && m == mcap) return true;
       int restarted = 0;
-      if (m == M) {
+      if (m == mcap) {
         k32_restart_coef<<<B, 32, 0, st>>>(y.ptr, yp.ptr, m, M, active.ptr, G.ptr);
         CU_LAUNCH_CHECK();
         k32_restart_vec<<<ge, 256, 0, st>>>(V.ptr, AV.ptr, m, M, L, y.ptr, yp.ptr, active.ptr);
@@ -1030,6 +1036,7 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
       extend(m, false, !restarted);
       m++;
     }
+    return false;
   };
   // the exact-point sigma: fused on the tensor cores where it fits (kpad <= 80)
   const bool exact_fused = sigma_exact_supported(bp.npair, bp.nstr);
@@ -1066,12 +1073,13 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
   };
 
   // stage A
-  stage(1, 150, 1, false, B);
+  stage(1, 150, 1, false, B, Ms);
   // refinement rounds
   const double abs_target = ctx->opt.conv_tol_r, rel_target = ctx->opt.mixed_rel_tol;
   k32_fill_i<<<1, 256, 0, st>>>(mask.ptr, B, 1);
   CU_LAUNCH_CHECK();
   std::vector<double> rn2(B);
+  int round_cap = Ms;
   for (int round = 0; round < 12; round++) {
     exact_point();
     // rnorm holds |r_x|^2 sums: take the square root on the host side copy
@@ -1100,7 +1108,9 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
     k32_save_yprev<<<B, 32, 0, st>>>(y.ptr, 1, M, 1, active.ptr, yp.ptr);
     CU_LAUNCH_CHECK();
     extend(1, true, false);
-    stage(2, 40, 0, true, na);
+    // a round that filled its subspace before its tuples reached the target
+    // (near-degenerate spaces) makes the later rounds use all M vectors
+    if (stage(2, 40, 0, true, na, round_cap)) round_cap = M;
   }
   if (sigma_tc_error(ctx, sw)) throw MbeError{MBE_ETIMEOUT, "tensor-core sigma wait timed out"};
 

@@ -363,6 +363,13 @@ bool sigma_tc_supported(int n, int nstr);
 void sigma_tc(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const float* c, int64_t c_stride,
               float* out, int64_t out_stride, const int32_t* active, double spin_shift);
 int32_t sigma_tc_error(mbe_ctx* ctx, SigmaWork& w);
+// subspace vectors allocated per tuple by the mixed Davidson: max_subspace
+// (clamped to 4..32) for its first stage and its refinement rounds, up to 12
+// more (at most 32) for the rounds after one that filled its subspace
+inline int mixed_subspace_alloc(int max_subspace) {
+  const int ms = max_subspace < 4 ? 4 : (max_subspace > 32 ? 32 : max_subspace);
+  return ms + 12 < 32 ? ms + 12 : 32;
+}
 // Davidson of the mixed-precision mode: FP32 vectors, FP64-grade exact points
 void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host,
                           int32_t* status_host, double* x_out_dev, const GuessPlan* plan);
