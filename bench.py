@@ -267,12 +267,20 @@ def transfer_bytes(res, h, eri):
 
 
 def mbe_opts(args) -> dict:
-    """--mbe-opt name=value overrides of mbe_options fields (ints or floats)."""
+    """--mbe-opt name=value overrides of mbe_options fields (ints or floats);
+    --tune-file PATH switches the autotuner on with that cache."""
     out = {}
     for item in args.mbe_opt or []:
         k, v = item.split("=", 1)
         out[k.strip()] = int(v) if v.strip().lstrip("-").isdigit() else float(v)
+    if getattr(args, "tune_file", None):
+        out["autotune"] = 1
+        out["tune_file"] = args.tune_file.encode()
     return out
+
+
+def opts_json(args) -> dict:
+    return {k: (v.decode() if isinstance(v, bytes) else v) for k, v in mbe_opts(args).items()}
 
 
 def run_profile_batch(args):
@@ -307,7 +315,7 @@ def run_profile_batch(args):
     torch.cuda.nvtx.range_pop()
     st = B.mbe_get_stats(m.ctx)
     print(json.dumps({"profile_batch": n, "cas": "6e/12o" if args.profile_small else "8e/12o",
-                      "options": mbe_opts(args), "seconds": dt, "tuples_per_s": n / dt,
+                      "options": opts_json(args), "seconds": dt, "tuples_per_s": n / dt,
                       "eps": [float(e) for e in eps],
                       "tc_tflops": st["dom_flops"] / st["dom_ms"] / 1e9 if st["dom_ms"] else None,
                       "stats": st}))
@@ -328,6 +336,8 @@ def main():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--mbe-opt", action="append", default=None, metavar="NAME=VALUE",
                     help="override an mbe_options field (repeatable), e.g. max_subspace=12")
+    ap.add_argument("--tune-file", default=None,
+                    help="autotune the two-spin tensor-core sigma, caching plans in this file")
     ap.add_argument("--fd-check", type=int, default=0,
                     help="finite-difference check of the energy gradient on this many "
                          "seeded unique integrals of the differentiation workload")
@@ -571,7 +581,8 @@ def main():
                            "l2": "256 MiB buffer written before each step (flushed); "
                                  "Davidson working set exceeds L2",
                            "parallelism": f"tuple-sharded x{world}" if world > 1 else "1 GPU",
-                           **({"options": mbe_opts(args)} if args.mbe_opt else {})},
+                           **({"options": opts_json(args)}
+                              if (args.mbe_opt or args.tune_file) else {})},
                 "sigma_tflops": {
                     "tensor_core": (st["dom_flops"] / (st["dom_ms"] * 1e-3) / 1e12)
                     if st["dom_ms"] else None,

@@ -141,7 +141,8 @@ typedef struct mbe_options {
                               (n, n_sigma) of the mixed mode times every
                               operand plan of the two-spin tensor-core kernel
                               that fits (A-operand stages 2..4, pull lists in
-                              shared or global memory) on its own data and
+                              shared or global memory, one or two epilogue
+                              groups) on its own data and
                               keeps the fastest for the shape; 0 (default):
                               the most stages that fit, lists in shared
                               memory when they fit.  All plans give the same
@@ -149,7 +150,7 @@ typedef struct mbe_options {
   const char* tune_file;   /* autotune cache (may be NULL): read at
                               mbe_create, one line per tuned shape appended
                               as it is tuned ("sigma_ab n nsig nstages
-                              pull_smem ms"); the string is copied           */
+                              pull_smem groups ms"); the string is copied    */
 } mbe_options;
 
 typedef struct mbe_ctx mbe_ctx;

@@ -352,16 +352,16 @@ int mbe_create(mbe_ctx** out, int device, const mbe_options* opt) {
   c->opt.tune_file = nullptr;   // the caller's string is not kept
   if (o.tune_file) {
     c->tune_file = o.tune_file;
-    // cached plans: "sigma_ab n nsig nstages pull_smem ms" per line
+    // cached plans: "sigma_ab n nsig nstages pull_smem groups ms" per line
     std::ifstream in(c->tune_file);
     std::string line;
     while (std::getline(in, line)) {
       std::istringstream ls(line);
       std::string tag;
-      int n = 0, ns = 0, nst = 0, ps = 0;
-      if (ls >> tag >> n >> ns >> nst >> ps && tag == "sigma_ab" && nst >= 2 && nst <= 4 &&
-          (ps == 0 || ps == 1))
-        c->tune_ab[{n, ns}] = {nst, ps};
+      int n = 0, ns = 0, nst = 0, ps = 0, ng = 0;
+      if (ls >> tag >> n >> ns >> nst >> ps >> ng && tag == "sigma_ab" && nst >= 2 && nst <= 4 &&
+          (ps == 0 || ps == 1) && (ng == 1 || ng == 2))
+        c->tune_ab[{n, ns}] = {nst, ps, ng};
     }
   }
   c->pool.cap = o.mem_cap_bytes;

@@ -4,6 +4,7 @@
 #include <stdint.h>
 #include <string>
 #include <vector>
+#include <array>
 #include <map>
 #include <memory>
 #include <unordered_map>
@@ -255,9 +256,9 @@ struct mbe_ctx {
   KeptRdm ref_ci;
   std::vector<RdmBlock> rdm_blocks;
   // autotuned operand plans of the two-spin tensor-core sigma:
-  // (n, nsig) -> (A stages, pull lists in shared memory); tune_file is the
-  // cache (empty: none)
-  std::map<std::pair<int, int>, std::pair<int, int>> tune_ab;
+  // (n, nsig) -> {A stages, pull lists in shared memory, epilogue groups};
+  // tune_file is the cache (empty: none)
+  std::map<std::pair<int, int>, std::array<int, 3>> tune_ab;
   std::string tune_file;
   // warm-start vectors of the previous and the current order
   GuessStore guess_prev, guess_cur;

@@ -40,6 +40,7 @@
 #include <cuda_bf16.h>
 #include <algorithm>
 #include <fstream>
+#include <cstdio>
 
 namespace {
 
@@ -352,10 +353,11 @@ struct AbLayout {
   uint32_t a, b, f, acc, pl, po, total, a_bytes, b_bytes;
   int fs;                              // row stride of the staged F tile (floats)
   int pull_smem;                       // 1: the pull lists are staged in shared memory
+  int ng;                              // epilogue groups (1 or 2)
 };
 
 __host__ __device__ inline AbLayout ab_layout(int kp, int kl, int nst, int nstr, int nlink,
-                                              int pull_smem) {
+                                              int pull_smem, int ng) {
   AbLayout L;
   uint32_t o = 0;
   auto take = [&](uint32_t bytes) {
@@ -368,10 +370,11 @@ __host__ __device__ inline AbLayout ab_layout(int kp, int kl, int nst, int nstr,
   L.b_bytes = (uint32_t)kl * kp * 2 * 2;
   L.fs = kp + 4;
   L.pull_smem = pull_smem;
+  L.ng = ng;
   L.a = take(L.a_bytes * nst);
   L.b = take(L.b_bytes * 2);
-  L.f = take((uint32_t)AB_M * L.fs * 4);
-  L.acc = take((uint32_t)nstr * 4);
+  L.f = take((uint32_t)AB_M * L.fs * 4 * ng);   // one staged tile per epilogue group
+  L.acc = take((uint32_t)nstr * 4 * 2);         // row sums of the even and odd tiles
   L.pl = pull_smem ? take((uint32_t)nstr * nlink * 2) : o;
   L.po = pull_smem ? take((uint32_t)nstr * (ntiles + 1) * 4) : o;
   L.total = o + 1024;   // alignment slack of the dynamic window
@@ -436,7 +439,7 @@ __device__ __forceinline__ int link_entry(int e0, int e1, int i) {
   return i < 32 ? s0 : s1;
 }
 
-template <int KP, bool PULL_SMEM>
+template <int KP, bool PULL_SMEM, int NG>
 __global__ void __launch_bounds__(AB_THREADS, 1)
 k_sigma_ab(const int32_t* __restrict__ lnk, const int16_t* __restrict__ plist,
            const int32_t* __restrict__ poff, int nstr, int nlink, int kl,
@@ -450,7 +453,7 @@ k_sigma_ab(const int32_t* __restrict__ lnk, const int16_t* __restrict__ plist,
       acc_full[2], acc_empty[2], mdone;
   __shared__ uint32_t tmem_sh;
   __shared__ int abort_sh;
-  const AbLayout L = ab_layout(KP, kl, nst, nstr, nlink, pull_smem);
+  const AbLayout L = ab_layout(KP, kl, nst, nstr, nlink, pull_smem, NG);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nitems = B * nstr, ntiles = (nstr + AB_M - 1) / AB_M;
   volatile int* abort_v = &abort_sh;
@@ -475,7 +478,7 @@ k_sigma_ab(const int32_t* __restrict__ lnk, const int16_t* __restrict__ plist,
       mbar_init(&full_b[s], 1);
       mbar_init(&empty_b[s], 1);
       mbar_init(&acc_full[s], 1);
-      mbar_init(&acc_empty[s], AB_EPI_WARPS);
+      mbar_init(&acc_empty[s], AB_EPI_WARPS / NG);
     }
     mbar_init(&mdone, 1);
     abort_sh = 0;
@@ -641,30 +644,41 @@ k_sigma_ab(const int32_t* __restrict__ lnk, const int16_t* __restrict__ plist,
     }
   } else {
     // ------------------------------------------------ stage F, pull into W
-    constexpr int NC = KP / 4;                 // pair columns staged per thread
-    const int e = warp - AB_EPI0, q = warp & 3, h = e >> 2;
+    // NG groups of the epilogue warps take the steps in turn (with two, group
+    // g the steps j with j % 2 == g, i.e. accumulator g), each with its own
+    // staged tile and row sums, so that one group's staging and pull overlap
+    // the other's
+    constexpr int GW = AB_EPI_WARPS / NG, GT = GW * 32;
+    constexpr int NC = KP * NG / 4;            // pair columns staged per thread
+    const int e = warp - AB_EPI0, g = e / GW, eg = e % GW;
+    const int q = warp & 3, h = eg >> 2;
     const int col0 = h * NC;
-    const int et = tid - AB_EPI0 * 32;
-    float* sF = reinterpret_cast<float*>(sm + L.f);
-    float* sAcc = reinterpret_cast<float*>(sm + L.acc);
+    const int et = tid - (AB_EPI0 + g * GW) * 32;   // thread within the group
+    float* sF = reinterpret_cast<float*>(sm + L.f) + g * AB_M * L.fs;
+    // the row's sums over its even and its odd tiles are kept apart and added
+    // at the end of the row (the same order whatever the group count)
+    float* sAccB = reinterpret_cast<float*>(sm + L.acc);
     const int16_t* PL = PULL_SMEM ? reinterpret_cast<const int16_t*>(sm + L.pl) : plist;
     const int32_t* PO = PULL_SMEM ? reinterpret_cast<const int32_t*>(sm + L.po) : poff;
     float* frow = sF + (32 * q + lane) * L.fs + col0;
     uint32_t j = 0;
     bool ok = true;
-    for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
       const int b = item / nstr, a = item - b * nstr;
       if (active && !active[b]) continue;
-      for (int t = 0; t < ntiles; t++, j++) {
-        const int sb = (int)(j & 1u);
-        const uint32_t pb = (j >> 1) & 1u;
-        // one thread waits for the accumulator; the others block in the
-        // barrier, which also tells that every thread has finished the
-        // previous step's pull (the staged tile may be overwritten)
+      // this group's first step in the row (steps alternate between groups)
+      const int t0 = NG == 1 ? 0 : (int)(((uint32_t)g - j) & 1u);
+      for (int t = t0; t < ntiles && ok; t += NG) {
+        const uint32_t jj = j + (uint32_t)t;
+        const int sb = (int)(jj & 1u);
+        const uint32_t pb = (jj >> 1) & 1u;
+        // one thread waits for the accumulator; the group's others block in
+        // the group barrier, which also tells that every thread of the group
+        // has finished its previous pull (the staged tile may be overwritten)
         const bool got = et == 0 ? mbar_wait_or_abort(&acc_full[sb], pb, wait_limit, abort_v,
                                                       AB_HINT_NS, AB_SLEEP_EPI)
                                  : true;
-        if (bar_red_or(1, AB_EPI_THREADS, !got)) {
+        if (bar_red_or(1 + g, GT, !got)) {
           ok = false;
           break;
         }
@@ -689,10 +703,12 @@ k_sigma_ab(const int32_t* __restrict__ lnk, const int16_t* __restrict__ plist,
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
         if (lane == 0) mbar_arrive(&acc_empty[sb]);
-        bar_sync_n(1, AB_EPI_THREADS);
+        bar_sync_n(1 + g, GT);
         // pull: W(a, J) += sum over the links of J into this tile, for J >= a
         // only (Z is symmetric: the lower triangle comes from the transpose)
-        for (int J = a + et; J < nstr; J += AB_EPI_THREADS) {
+        float* sAcc = sAccB + (NG == 1 ? (t & 1) : g) * nstr;
+        const bool first = NG == 1 ? t < 2 : t == t0;
+        for (int J = a + et; J < nstr; J += GT) {
           const int32_t* po = PO + J * (ntiles + 1) + t;
           const int lo = po[0], hi = po[1];
           const int16_t* pl = PL + J * nlink;
@@ -717,15 +733,35 @@ k_sigma_ab(const int32_t* __restrict__ lnk, const int16_t* __restrict__ plist,
             s0 += __int_as_float(__float_as_int(sF[en & 0x7FFF]) ^ ((en & 0x8000) << 16));
           }
           const float s = s0 + s1;
-          sAcc[J] = t ? sAcc[J] + s : s;
+          sAcc[J] = first ? s : sAcc[J] + s;
         }
       }
-      if (!ok) break;
+      j += (uint32_t)ntiles;
+      // two groups meet at the end of the row (also after a failed wait, so
+      // that neither is left waiting for the other); one group's threads
+      // already agree (its barrier), and each reads only the sums it wrote
+      if (NG == 2) {
+        if (bar_red_or(3, AB_EPI_THREADS, !ok)) {
+          ok = false;
+          break;
+        }
+      } else if (!ok) {
+        break;
+      }
       // F carries g'/2: the upper triangle takes Z(a, J) = 2 (F pulled), the
-      // diagonal Z(a, a) / 2, so that sigma = W + W^T holds Z once
+      // diagonal Z(a, a) / 2, so that sigma = W + W^T holds Z once; the two
+      // groups' sums of each J are added by one thread of either group
+      const bool two = ntiles > 1;                      // odd tiles summed too
+      // the array of the even tiles: 0, or the group that had step t = 0
+      const int ev = NG == 1 ? 0 : (int)((j - (uint32_t)ntiles) & 1u);
       float* wr = W + (int64_t)b * w_stride + (int64_t)a * nstr;
-      for (int J = a + et; J < nstr; J += AB_EPI_THREADS)
-        wr[J] += J > a ? 2.f * sAcc[J] : sAcc[J];
+      for (int J = a + e * 32 + lane; J < nstr; J += AB_EPI_THREADS) {
+        float v = sAccB[ev * nstr + J];
+        if (two) v += sAccB[(ev ^ 1) * nstr + J];
+        wr[J] += J > a ? 2.f * v : v;
+      }
+      // the sums are read before either group overwrites them in the next row
+      if (NG == 2) bar_sync_n(3, AB_EPI_THREADS);
     }
     if (!ok && et == 0) {
       *abort_v = 1;
@@ -805,8 +841,14 @@ struct AbPlan {
 // barriers
 constexpr uint32_t AB_SMEM_MAX = 224 * 1024;
 
-// operand plan of k_sigma_ab: the most A stages (4 down to 2) that fit, and
-// the pull lists in shared memory if they fit beside them
+// operand plan of k_sigma_ab, the first that fits of: the pull lists in
+// shared memory with 4, then 3 A stages (two epilogue groups before one),
+// the lists in global memory likewise, then 2 stages.  Measured on the
+// order-6 bins of the 8e/23o workload (autotuner, 64 tuples): for 8e/12o the
+// lists in shared memory matter most (one group, 4 stages, lists in shared
+// memory 1.24 ms; two groups only fit with the lists in global memory,
+// 1.28 ms at best); for 6e/12o, where both fit, two groups win (0.25 against
+// 0.32 ms)
 inline bool ab_plan(int n, int nsig, int nstr, AbPlan& p) {
   const int npair = n * (n + 1) / 2;
   p.kp = round_up(npair, 16);
@@ -814,37 +856,40 @@ inline bool ab_plan(int n, int nsig, int nstr, AbPlan& p) {
   p.kl = round_up(std::max(p.nlink, 1), 16);
   p.ldc = round_up(nstr, 8);
   if (p.kp > 128 || p.kl > 64 || nstr > AB_NSTR_MAX) return false;
-  for (p.nst = AB_MAX_STAGES; p.nst >= 2; p.nst--)
-    for (int ps = 1; ps >= 0; ps--) {
-      p.L = ab_layout(p.kp, p.kl, p.nst, nstr, p.nlink, ps);
-      if (p.L.total <= AB_SMEM_MAX) return true;
-    }
+  static const int order[][3] = {  // {pull lists in shared memory, stages, groups}
+      {1, 4, 2}, {1, 4, 1}, {1, 3, 2}, {1, 3, 1}, {0, 4, 2}, {0, 3, 2}, {0, 4, 1},
+      {0, 3, 1}, {1, 2, 2}, {1, 2, 1}, {0, 2, 2}, {0, 2, 1}};
+  for (const auto& o : order) {
+    p.nst = o[1];
+    p.L = ab_layout(p.kp, p.kl, p.nst, nstr, p.nlink, o[0], o[2]);
+    if (p.L.total <= AB_SMEM_MAX) return true;
+  }
   return false;
 }
 
-// a given operand plan (nst A stages, pull lists in shared memory or not),
-// if its layout fits
-inline bool ab_plan_with(int n, int nsig, int nstr, int nst, int ps, AbPlan& p) {
+// a given operand plan (nst A stages, pull lists in shared memory or not, ng
+// epilogue groups), if its layout fits
+inline bool ab_plan_with(int n, int nsig, int nstr, int nst, int ps, int ng, AbPlan& p) {
   if (!ab_plan(n, nsig, nstr, p)) return false;
-  if (nst < 2 || nst > AB_MAX_STAGES) return false;
+  if (nst < 2 || nst > AB_MAX_STAGES || ng < 1 || ng > 2) return false;
   p.nst = nst;
-  p.L = ab_layout(p.kp, p.kl, p.nst, nstr, p.nlink, ps);
+  p.L = ab_layout(p.kp, p.kl, p.nst, nstr, p.nlink, ps, ng);
   return p.L.total <= AB_SMEM_MAX && p.L.pull_smem == (ps != 0);
 }
 
-template <int KP, bool PS>
+template <int KP, bool PS, int NG>
 void launch_ab_kps(int device, int grid, const AbPlan& p, cudaStream_t st, const int32_t* lnk,
                    const int16_t* plist, const int32_t* poff, int nstr, const bf16* gh,
                    const bf16* cs, int64_t cs_stride, const int32_t* active, int B, float* W,
                    int64_t w_stride, long long wait_limit, int32_t* err) {
   static bool attr_done[MBE_MAX_DEVICES] = {false};
   once_per_device(attr_done, device, [] {
-    CU_CHECK(cudaFuncSetAttribute(k_sigma_ab<KP, PS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)AB_SMEM_MAX));
+    CU_CHECK(cudaFuncSetAttribute(k_sigma_ab<KP, PS, NG>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AB_SMEM_MAX));
   });
-  k_sigma_ab<KP, PS><<<grid, AB_THREADS, p.L.total, st>>>(lnk, plist, poff, nstr, p.nlink, p.kl,
-                                                          gh, cs, cs_stride, p.ldc, active, B,
-                                                          p.nst, W, w_stride, wait_limit, err);
+  k_sigma_ab<KP, PS, NG><<<grid, AB_THREADS, p.L.total, st>>>(
+      lnk, plist, poff, nstr, p.nlink, p.kl, gh, cs, cs_stride, p.ldc, active, B, p.nst, W,
+      w_stride, wait_limit, err);
 }
 
 template <int KP>
@@ -852,12 +897,17 @@ void launch_ab_kp(int device, int grid, const AbPlan& p, cudaStream_t st, const 
                   const int16_t* plist, const int32_t* poff, int nstr, const bf16* gh,
                   const bf16* cs, int64_t cs_stride, const int32_t* active, int B, float* W,
                   int64_t w_stride, long long wait_limit, int32_t* err) {
-  if (p.L.pull_smem)
-    launch_ab_kps<KP, true>(device, grid, p, st, lnk, plist, poff, nstr, gh, cs, cs_stride, active,
-                            B, W, w_stride, wait_limit, err);
-  else
-    launch_ab_kps<KP, false>(device, grid, p, st, lnk, plist, poff, nstr, gh, cs, cs_stride,
-                             active, B, W, w_stride, wait_limit, err);
+#define MBE_AB_KPS(PS, NG)                                                                \
+  launch_ab_kps<KP, PS, NG>(device, grid, p, st, lnk, plist, poff, nstr, gh, cs, cs_stride, \
+                            active, B, W, w_stride, wait_limit, err)
+  if (p.L.ng == 2) {
+    if (p.L.pull_smem) MBE_AB_KPS(true, 2);
+    else MBE_AB_KPS(false, 2);
+  } else {
+    if (p.L.pull_smem) MBE_AB_KPS(true, 1);
+    else MBE_AB_KPS(false, 1);
+  }
+#undef MBE_AB_KPS
 }
 
 void launch_ab(int device, int grid, const AbPlan& p, cudaStream_t st, const int32_t* lnk,
@@ -919,7 +969,7 @@ void sigma_tc(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const float* c, int64_
     AbPlan q;
     if (it == ctx->tune_ab.end())
       tune_now = true;
-    else if (ab_plan_with(bp.n, bp.nsig, nstr, it->second.first, it->second.second, q))
+    else if (ab_plan_with(bp.n, bp.nsig, nstr, it->second[0], it->second[1], it->second[2], q))
       p = q;
   }
   const int64_t N = bp.ndet;
@@ -989,11 +1039,12 @@ void sigma_tc(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const float* c, int64_
     CU_CHECK(cudaEventCreate(&e0));
     CU_CHECK(cudaEventCreate(&e1));
     float best = 1e30f;
-    int best_nst = p.nst, best_ps = p.L.pull_smem ? 1 : 0;
+    int best_nst = p.nst, best_ps = p.L.pull_smem ? 1 : 0, best_ng = p.L.ng;
+    for (int ng = 1; ng <= 2; ng++)
     for (int nst = 2; nst <= AB_MAX_STAGES; nst++)
       for (int ps = 0; ps <= 1; ps++) {
         AbPlan q;
-        if (!ab_plan_with(bp.n, bp.nsig, nstr, nst, ps, q)) continue;
+        if (!ab_plan_with(bp.n, bp.nsig, nstr, nst, ps, ng, q)) continue;
         float t = 1e30f;
         for (int rep = 0; rep < 3; rep++) {
           k_gemm_haa<<<dim3(nt_g * nt_g, B), G_THREADS, G_SMEM, st>>>(
@@ -1010,21 +1061,25 @@ void sigma_tc(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const float* c, int64_
           CU_CHECK(cudaEventElapsedTime(&ms, e0, e1));
           if (rep > 0) t = std::min(t, ms);
         }
+        if (ctx->opt.verbose)
+          fprintf(stderr, "[mbe autotune] n=%d nsig=%d stages=%d pull_smem=%d groups=%d %.4f ms\n",
+                  bp.n, bp.nsig, nst, ps, ng, t);
         if (t < best) {
           best = t;
           best_nst = nst;
           best_ps = ps;
+          best_ng = ng;
         }
       }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    ctx->tune_ab[{bp.n, bp.nsig}] = {best_nst, best_ps};
+    ctx->tune_ab[{bp.n, bp.nsig}] = {best_nst, best_ps, best_ng};
     AbPlan q;
-    if (ab_plan_with(bp.n, bp.nsig, nstr, best_nst, best_ps, q)) p = q;
+    if (ab_plan_with(bp.n, bp.nsig, nstr, best_nst, best_ps, best_ng, q)) p = q;
     if (!ctx->tune_file.empty()) {
       std::ofstream out(ctx->tune_file, std::ios::app);
       out << "sigma_ab " << bp.n << " " << bp.nsig << " " << best_nst << " " << best_ps << " "
-          << best << "\n";
+          << best_ng << " " << best << "\n";
     }
   }
   cudaEvent_t ev;

@@ -41,11 +41,12 @@ def test_autotune_same_bits_and_cache(lib, tmp_path):
     assert np.all(st_def == 0) and np.all(st_tun == 0)
     assert np.array_equal(e_def, e_tun)
     lines = [ln.split() for ln in cache.read_text().splitlines() if ln.strip()]
-    assert lines and all(ln[0] == "sigma_ab" and len(ln) == 6 for ln in lines)
+    assert lines and all(ln[0] == "sigma_ab" and len(ln) == 7 for ln in lines)
     shapes = {(int(ln[1]), int(ln[2])) for ln in lines}
     assert len(shapes) == len(lines)
     for ln in lines:
-        assert 2 <= int(ln[3]) <= 4 and int(ln[4]) in (0, 1) and float(ln[5]) > 0.0
+        assert 2 <= int(ln[3]) <= 4 and int(ln[4]) in (0, 1) and int(ln[5]) in (1, 2)
+        assert float(ln[6]) > 0.0
     # a second context reads the cache: nothing is tuned again
     e_again, _ = _solve(lib, h, eri, nocc, ref, tuples, autotune=1,
                         tune_file=str(cache).encode())
