@@ -45,8 +45,8 @@ DEFAULT_WORKLOAD = "h2o_dz_8e23o"
 # profiles/k_sigma_ab_8e12o_batch64.md.
 TRAFFIC = {"k_gemm_haa": {"bytes_per_flop": (125788672 + 37701376) / 1.9081e11,
                           "sha": "fc8f06c321a2b658"},
-           "k_sigma_ab": {"bytes_per_flop": (100036352 + 12476160) / 1.9081e11,
-                          "sha": "c70ddd0661db1d35"}}
+           "k_sigma_ab": {"bytes_per_flop": (99887872 + 9439744) / 1.9081e11,
+                          "sha": "a498f9b7eb8ce26f"}}
 
 
 def peaks():
