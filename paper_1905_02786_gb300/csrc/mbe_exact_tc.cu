@@ -35,7 +35,7 @@ namespace {
 
 using namespace tc5;
 
-constexpr int EX_THREADS = 256;
+constexpr int EX_THREADS = 512;
 constexpr int EX_M = 128;
 constexpr int EX_SLICES = 5;
 constexpr int EX_GROUPS = 6;
@@ -229,8 +229,8 @@ k_sigma_exact(const int32_t* __restrict__ link, int nstr, int npair, int kpad,
   uint32_t phase = 0;
   bool ok = true;
 
-  // thread -> determinant m = tid % 128 and P-blocks tid / 128 + 2 i (gather),
-  // warp -> TMEM lanes 32 (w mod 4) and 8-column chunks w / 4 + 2 i (epilogue)
+  // thread -> determinant m = tid % 128 and P-blocks tid / 128 + 4 i (gather),
+  // warp -> TMEM lanes 32 (w mod 4) and 8-column chunks w / 4 + 4 i (epilogue)
   const int gm = tid & (EX_M - 1);
   const int gr = gm / W, gj = gm % W;
   const int ga = a0 + gr;
@@ -280,7 +280,7 @@ k_sigma_exact(const int32_t* __restrict__ link, int nstr, int npair, int kpad,
     // ---- pass 1: e_m from max_P (|d_1| + |d_2|)
     {
       int e = -1000;
-      for (int kb = tid >> 7; kb < nkb; kb += 2) {
+      for (int kb = tid >> 7; kb < nkb; kb += EX_THREADS / EX_M) {
         float d1[8], d2[8];
         terms(k, col_ok, kb * 8, lkg, d1, d2);
 #pragma unroll
@@ -292,7 +292,7 @@ k_sigma_exact(const int32_t* __restrict__ link, int nstr, int npair, int kpad,
     // ---- pass 2: digit planes of D (A operand)
     {
       const int e = sEm[gm];
-      for (int kb = tid >> 7; kb < nkb; kb += 2) {
+      for (int kb = tid >> 7; kb < nkb; kb += EX_THREADS / EX_M) {
         float d1[8], d2[8];
         terms(k, col_ok, kb * 8, lkg, d1, d2);
         __align__(16) __nv_bfloat16 sl[EX_SLICES][8];
@@ -350,7 +350,7 @@ k_sigma_exact(const int32_t* __restrict__ link, int nstr, int npair, int kpad,
       const uint16_t* lke = sLk + ej * LS;
       const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
 #pragma unroll 1
-      for (int ch = warp >> 2; ch < nkb; ch += 2) {
+      for (int ch = warp >> 2; ch < nkb; ch += EX_THREADS / EX_M) {
         long long I[8];
 #pragma unroll
         for (int q = 0; q < 8; q++) I[q] = 0;
