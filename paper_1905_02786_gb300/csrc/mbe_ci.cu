@@ -533,40 +533,52 @@ __global__ void k_finish_sym_fp64(double* __restrict__ out, int64_t out_stride,
     }
   }
   __syncthreads();
-  for (int h = 0; h < 2; h++) {
-    const int r0 = (h ? J : I) * 32, c0 = (h ? I : J) * 32;
-    for (int i = ty; i < 32; i += blockDim.x >> 5) {
-      const int ia = r0 + i, ib = c0 + tx;
-      if (ia >= nstr || ib >= nstr) continue;
-      const int64_t idx = (int64_t)ia * nstr + ib;
-      double v = sX[h][i][tx] + sX[1 - h][tx][i];
-      if (shift != 0.0) {
-        // evaluated for (min, max): bitwise the same for both elements
-        const int lo = min(ia, ib), hi = max(ia, ib);
-        const int32_t* la = link + (int64_t)lo * npair;
-        const int32_t* lb = link + (int64_t)hi * npair;
-        const uint32_t ma = masks[lo], mb = masks[hi];
-        double s2 = (double)(nsig - __popc(ma & mb)) * cb[(int64_t)lo * nstr + hi];
-        uint32_t oa = ma & ~mb;
-        const uint32_t obm = mb & ~ma;
-        while (oa) {
-          const int q = __ffs(oa) - 1;
-          oa &= oa - 1;
-          uint32_t o2 = obm;
-          while (o2) {
-            const int p = __ffs(o2) - 1;
-            o2 &= o2 - 1;
-            const int P = p > q ? p * (p + 1) / 2 + q : q * (q + 1) / 2 + p;
-            const int32_t ta = la[P], tb = lb[P];
-            const double x = cb[(int64_t)(ta >> 1) * nstr + (tb >> 1)];
-            s2 -= ((ta ^ tb) & 1) ? -x : x;
-          }
+  // sigma is symmetric: the values of tile (I, J) are formed once and
+  // written to both tiles (the transpose through shared memory)
+  const int ny = blockDim.x >> 5;
+  double v[4];
+  for (int k = 0, i = ty; i < 32; i += ny, k++) {
+    const int ia = I * 32 + i, ib = J * 32 + tx;
+    double s = sX[0][i][tx] + sX[1][tx][i];
+    if (shift != 0.0 && ia < nstr && ib < nstr) {
+      // evaluated for (min, max): bitwise the same for both elements
+      const int lo = min(ia, ib), hi = max(ia, ib);
+      const int32_t* la = link + (int64_t)lo * npair;
+      const int32_t* lb = link + (int64_t)hi * npair;
+      const uint32_t ma = masks[lo], mb = masks[hi];
+      double s2 = (double)(nsig - __popc(ma & mb)) * cb[(int64_t)lo * nstr + hi];
+      uint32_t oa = ma & ~mb;
+      const uint32_t obm = mb & ~ma;
+      while (oa) {
+        const int q = __ffs(oa) - 1;
+        oa &= oa - 1;
+        uint32_t o2 = obm;
+        while (o2) {
+          const int p = __ffs(o2) - 1;
+          o2 &= o2 - 1;
+          const int P = p > q ? p * (p + 1) / 2 + q : q * (q + 1) / 2 + p;
+          const int32_t ta = la[P], tb = lb[P];
+          const double x = cb[(int64_t)(ta >> 1) * nstr + (tb >> 1)];
+          s2 -= ((ta ^ tb) & 1) ? -x : x;
         }
-        v += shift * s2;
       }
-      ob[idx] = v;
+      s += shift * s2;
     }
-    if (I == J) break;
+    v[k] = s;
+  }
+  // every read of tile (I, J) and (J, I) went through shared memory above;
+  // the CTA owns both tiles, so the in-place stores race with nothing
+  for (int k = 0, i = ty; i < 32; i += ny, k++) {
+    const int ia = I * 32 + i, ib = J * 32 + tx;
+    if (ia < nstr && ib < nstr) ob[(int64_t)ia * nstr + ib] = v[k];
+  }
+  if (I == J) return;
+  __syncthreads();
+  for (int k = 0, i = ty; i < 32; i += ny, k++) sX[0][i][tx] = v[k];
+  __syncthreads();
+  for (int i = ty; i < 32; i += ny) {
+    const int ia = J * 32 + i, ib = I * 32 + tx;
+    if (ia < nstr && ib < nstr) ob[(int64_t)ia * nstr + ib] = sX[0][tx][i];
   }
 }
 

@@ -777,34 +777,47 @@ k_sigma_ab(const int32_t* __restrict__ lnk, const int16_t* __restrict__ plist,
 
 // sigma(a,b) = W(a,b) + W(b,a) + shift (S^2 c)(a,b), FP32 output.  For
 // Ms = 0, S^2 = S- S+ gives (S^2 c)(a, b) = (n_sigma - |a & b|) c(a, b) -
-// sum over q in a\b, p in b\a of the signed c(a - q + p, b - p + q)
+// sum over q in a\b, p in b\a of the signed c(a - q + p, b - p + q).
+// sigma is symmetric: one CTA per 32 x 32 tile pair (I, J), I <= J, forms
+// the values of tile (I, J) once (the spin term's gathers of c are the cost
+// of this kernel) and writes them to both tiles, the transpose through
+// shared memory so that every store is coalesced.
 __global__ void k_sigma_tc_finish(const float* __restrict__ X, int64_t x_stride,
                                   const int32_t* __restrict__ link, const uint32_t* __restrict__ masks,
                                   int nstr, int n, int nsig, const float* __restrict__ c,
                                   int64_t c_stride, float shift, const int32_t* __restrict__ active,
                                   float* __restrict__ out, int64_t out_stride) {
-  const int b = blockIdx.z;
+  const int b = blockIdx.y;
   if (active && !active[b]) return;
-  // 32 x 32 tile with its transpose staged in shared memory
-  __shared__ float tT[32][33];
-  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  const int nt = (nstr + 31) / 32;
+  int t = blockIdx.x, I = 0;
+  while (t >= nt - I) {
+    t -= nt - I;
+    I++;
+  }
+  const int J = I + t;
+  __shared__ float sX[2][32][33];
   const float* Xb = X + (int64_t)b * x_stride;
-  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-    const int row = bx + i, col = by + threadIdx.x;     // element (bx+i, by+tx) of X
-    tT[threadIdx.x][i] = (row < nstr && col < nstr) ? Xb[(int64_t)row * nstr + col] : 0.f;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, ny = blockDim.x >> 5;
+  // sX[0] = tile (I, J) of W, sX[1] = tile (J, I)
+  for (int h = 0; h < 2; h++) {
+    const int r0 = (h ? J : I) * 32, c0 = (h ? I : J) * 32;
+    for (int i = ty; i < 32; i += ny) {
+      const int row = r0 + i, col = c0 + tx;
+      sX[h][i][tx] = (row < nstr && col < nstr) ? Xb[(int64_t)row * nstr + col] : 0.f;
+    }
   }
   __syncthreads();
   const int npair = n * (n + 1) / 2;
   const float* cb = c + (int64_t)b * c_stride;
   float* ob = out + (int64_t)b * out_stride;
-  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-    const int ia = by + i, ib = bx + threadIdx.x;       // output (ia, ib): X(ia,ib) + X(ib,ia)
-    if (ia >= nstr || ib >= nstr) continue;
-    const int64_t idx = (int64_t)ia * nstr + ib;
-    float v = Xb[idx] + tT[i][threadIdx.x];
-    if (shift != 0.f) {
-      // (S^2 c)(a, b) = (S^2 c)(b, a) for symmetric c: evaluate it for
-      // (min, max) so that both elements get bitwise the same value
+  float v[4];
+  for (int k = 0, i = ty; i < 32; i += ny, k++) {
+    const int ia = I * 32 + i, ib = J * 32 + tx;    // element (ia, ib) and its transpose
+    float s = sX[0][i][tx] + sX[1][tx][i];
+    if (shift != 0.f && ia < nstr && ib < nstr) {
+      // evaluated for (min, max): on the diagonal tile both elements of a
+      // pair get bitwise the same value
       const int lo = min(ia, ib), hi = max(ia, ib);
       const int32_t* la = link + (int64_t)lo * npair;
       const int32_t* lb = link + (int64_t)hi * npair;
@@ -826,9 +839,18 @@ __global__ void k_sigma_tc_finish(const float* __restrict__ X, int64_t x_stride,
           s2 -= ((ta ^ tb) & 1) ? -x : x;
         }
       }
-      v += shift * s2;
+      s += shift * s2;
     }
-    ob[idx] = v;
+    v[k] = s;
+    if (ia < nstr && ib < nstr) ob[(int64_t)ia * nstr + ib] = s;
+  }
+  if (I == J) return;                                // the tile was its own transpose
+  __syncthreads();
+  for (int k = 0, i = ty; i < 32; i += ny, k++) sX[0][i][tx] = v[k];
+  __syncthreads();
+  for (int i = ty; i < 32; i += ny) {
+    const int ia = J * 32 + i, ib = I * 32 + tx;
+    if (ia < nstr && ib < nstr) ob[(int64_t)ia * nstr + ib] = sX[0][tx][i];
   }
 }
 
@@ -1101,8 +1123,8 @@ void sigma_tc(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const float* c, int64_
   }
   ctx->dom_timer.end(st, ev);
   ctx->stats.dom_launches += 1;
-  dim3 g2((unsigned)((nstr + 31) / 32), (unsigned)((nstr + 31) / 32), B);
-  k_sigma_tc_finish<<<g2, dim3(32, 8), 0, st>>>(w.Xf.ptr, N, bp.tab->link.ptr, bp.tab->masks.ptr,
+  const int ntl = (nstr + 31) / 32;
+  k_sigma_tc_finish<<<dim3((unsigned)(ntl * (ntl + 1) / 2), B), 256, 0, st>>>(w.Xf.ptr, N, bp.tab->link.ptr, bp.tab->masks.ptr,
                                                 nstr, bp.n, bp.nsig, c, c_stride,
                                                 (float)spin_shift, active, out, out_stride);
   CU_LAUNCH_CHECK();
