@@ -600,7 +600,9 @@ def main():
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "measured_fp_peaks": fp_peaks,
                 "mixed_vs_fp64_gpu": cmp,
-                "gpu_launches": int(st["launches"]), "clocks": clk,
+                "gpu_launches": int(st["launches"]),
+                "host_launches": int(st["host_launches"]),
+                "graph_launches": int(st["graph_launches"]), "clocks": clk,
                 "total_energy": res["total"]}
         print(json.dumps(line), flush=True)
     m.close()

@@ -151,6 +151,13 @@ typedef struct mbe_options {
                               mbe_create, one line per tuned shape appended
                               as it is tuned ("sigma_ab n nsig nstages
                               pull_smem groups ms"); the string is copied    */
+  int graphs;              /* mixed mode: 1 (default) issues each Davidson
+                              iteration (sigma vector, subspace update, Ritz
+                              step, residual, correction and its
+                              orthogonalisation) as one CUDA graph, captured
+                              from the stream and replayed through an
+                              executable graph updated in place; 0: plain
+                              stream launches.  Same kernels, same bits.    */
 } mbe_options;
 
 typedef struct mbe_ctx mbe_ctx;
@@ -164,7 +171,8 @@ typedef struct mbe_stats {
   int64_t iters_total;    /* Davidson iterations summed over CASCIs           */
   int64_t iters_max;      /* largest iteration count of one CASCI             */
   int64_t noconv;         /* CASCIs that hit the iteration cap                */
-  int64_t launches;       /* kernel launches issued by the library            */
+  int64_t launches;       /* kernels the library ran on the device (those of
+                             replayed CUDA graphs included)                   */
   int64_t dom_launches;   /* launches of the fused tensor-core sigma kernel   */
   double dom_ms;          /* their summed device time (CUDA events on the
                              context stream); 0 unless opt.timing = 1         */
@@ -173,12 +181,17 @@ typedef struct mbe_stats {
   int64_t fp64_launches;  /* launches of the FP64 (kl|ij) contraction kernel  */
   double fp64_ms;         /* their summed device time (opt.timing = 1)        */
   double fp64_flops;      /* their algorithmic flops                          */
+  int64_t host_launches;  /* launch calls the host made: kernel launches
+                             outside graphs plus graph launches               */
+  int64_t graph_launches; /* CUDA graph launches (opt.graphs)                 */
+  int64_t graph_builds;   /* graphs instantiated (the others were updated in
+                             place before their launch)                       */
 } mbe_stats;
 
 /* Fill *opt with the defaults (FP64, max_batch 256, subspace 20, 400
  * iterations, tol_r 1e-8, tol_e 1e-12, spin_shift 0.5, keep_ci 0,
  * deterministic 1, no memory cap, warm_start 0, mixed schedule 1e-5 / 1e-2 /
- * 2e-7, pspace 128, wait_limit 2^24). */
+ * 2e-7, pspace 128, wait_limit 2^24, autotune 0, graphs 1). */
 void mbe_default_options(mbe_options* opt);
 
 /* Create a context on CUDA device `device`.  opt may be NULL (defaults).

@@ -46,7 +46,7 @@ class mbe_options(ctypes.Structure):
                 ("mixed_stage_tol", ctypes.c_double), ("mixed_round_drop", ctypes.c_double),
                 ("mixed_rel_tol", ctypes.c_double), ("pspace", ctypes.c_int),
                 ("wait_limit", ctypes.c_int64), ("autotune", ctypes.c_int),
-                ("tune_file", ctypes.c_char_p)]
+                ("tune_file", ctypes.c_char_p), ("graphs", ctypes.c_int)]
 
 
 _lib = None
@@ -282,7 +282,8 @@ class mbe_stats(ctypes.Structure):
                 ("launches", ctypes.c_int64), ("dom_launches", ctypes.c_int64),
                 ("dom_ms", ctypes.c_double), ("dom_flops", ctypes.c_double),
                 ("fp64_launches", ctypes.c_int64), ("fp64_ms", ctypes.c_double),
-                ("fp64_flops", ctypes.c_double)]
+                ("fp64_flops", ctypes.c_double), ("host_launches", ctypes.c_int64),
+                ("graph_launches", ctypes.c_int64), ("graph_builds", ctypes.c_int64)]
 
 
 def mbe_set_order_energies(ctx, tuples, eps, order: int | None = None):

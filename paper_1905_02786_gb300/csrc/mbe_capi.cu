@@ -10,6 +10,9 @@
 #include <set>
 
 int64_t g_mbe_launches = 0;
+int64_t g_mbe_host_launches = 0;
+thread_local bool t_capturing = false;
+thread_local int64_t t_capture_kernels = 0;
 
 // ------------------------------------------------------------ DevPool
 void* DevPool::alloc(size_t bytes) {
@@ -322,6 +325,7 @@ void mbe_default_options(mbe_options* o) {
   o->wait_limit = 1LL << 24;
   o->autotune = 0;
   o->tune_file = nullptr;
+  o->graphs = 1;
 }
 
 int mbe_create(mbe_ctx** out, int device, const mbe_options* opt) {
@@ -337,7 +341,7 @@ int mbe_create(mbe_ctx** out, int device, const mbe_options* opt) {
     return MBE_EINVAL;
   if (!(o.mixed_stage_tol > 0.0) || !(o.mixed_round_drop > 0.0 && o.mixed_round_drop < 1.0) ||
       !(o.mixed_rel_tol > 0.0) || o.pspace < 0 || o.pspace > 128 || o.wait_limit < 0 ||
-      (o.autotune != 0 && o.autotune != 1))
+      (o.autotune != 0 && o.autotune != 1) || (o.graphs != 0 && o.graphs != 1))
     return MBE_EINVAL;
   int ndev = 0;
   if (device < 0 || device >= MBE_MAX_DEVICES) return MBE_EINVAL;
@@ -767,6 +771,8 @@ int mbe_get_stats(const mbe_ctx* ctx, mbe_stats* out) {
   c->fp64_timer.resolve();
   *out = ctx->stats;
   out->launches = __atomic_load_n(&g_mbe_launches, __ATOMIC_RELAXED) - ctx->launch_base;
+  out->host_launches =
+      __atomic_load_n(&g_mbe_host_launches, __ATOMIC_RELAXED) - ctx->host_launch_base;
   out->dom_ms = c->dom_timer.ms;
   out->fp64_ms = c->fp64_timer.ms;
   return MBE_OK;
@@ -781,6 +787,7 @@ int mbe_reset_stats(mbe_ctx* ctx) {
   ctx->fp64_timer.ms = 0.0;
   ctx->stats = mbe_stats{};
   ctx->launch_base = __atomic_load_n(&g_mbe_launches, __ATOMIC_RELAXED);
+  ctx->host_launch_base = __atomic_load_n(&g_mbe_host_launches, __ATOMIC_RELAXED);
   return MBE_OK;
 }
 

@@ -784,7 +784,8 @@ __global__ void k32_exact_fin(const double* __restrict__ xax, const double* __re
 
 // target of tuple b: max(abs_target, rel_target max(1, |theta_x|)); the FP32
 // storage of x puts a floor of a few 1e-8 |A| on its exact residual
-__global__ void k32_select(const double* __restrict__ rnorm, const int32_t* __restrict__ mask,
+// rnorm of the tuples in `mask` arrives as |r_x|^2 and leaves as |r_x|
+__global__ void k32_select(double* __restrict__ rnorm, const int32_t* __restrict__ mask,
                            const double* __restrict__ thx, int B, double abs_target,
                            double rel_target, double drop, int32_t* __restrict__ active,
                            double* __restrict__ tolr, int32_t* __restrict__ nactive) {
@@ -793,9 +794,14 @@ __global__ void k32_select(const double* __restrict__ rnorm, const int32_t* __re
   __syncthreads();
   for (int b = threadIdx.x; b < B; b += blockDim.x) {
     const double target = fmax(abs_target, rel_target * fmax(1.0, fabs(thx[b])));
-    const int a = (mask[b] && rnorm[b] > target) ? 1 : 0;
+    double r = rnorm[b];
+    if (mask[b]) {
+      r = sqrt(fmax(0.0, r));
+      rnorm[b] = r;
+    }
+    const int a = (mask[b] && r > target) ? 1 : 0;
     active[b] = a;
-    tolr[b] = fmax(target, drop * rnorm[b]);
+    tolr[b] = fmax(target, drop * r);
     if (a) atomicAdd(&cnt, 1);
   }
   __syncthreads();
@@ -991,51 +997,99 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
   // when the subspace is full)
   // returns true when an exact0 stage ended because its subspace (mcap
   // vectors) was full with tuples still iterating
+  //
+  // An iteration is a head (sigma vector of V[m-1], subspace row, Ritz
+  // step, residual and correction, convergence flags), one synchronisation
+  // (the number of tuples still iterating), then a tail (restart when the
+  // subspace is full, the next vector V[m]).  The tail is issued together
+  // with the next head, so that with opt.graphs one CUDA graph per
+  // iteration carries both: the host makes one launch and one
+  // synchronisation per iteration.  The graph's shape depends only on
+  // (exact0, tail present, restart); m changes pointers and loop bounds,
+  // which the in-place update of the executable graph takes.
+  // (the legacy default stream cannot be captured: plain launches there)
+  const bool use_graphs = ctx->opt.graphs != 0 && st != nullptr && st != cudaStreamLegacy;
+  GraphRunner gr(st);
+  auto tail = [&](int m_full, bool restart) {
+    int m = m_full;
+    if (restart) {
+      k32_restart_coef<<<B, 32, 0, st>>>(y.ptr, yp.ptr, m, M, active.ptr, G.ptr);
+      CU_LAUNCH_CHECK();
+      k32_restart_vec<<<ge, 256, 0, st>>>(V.ptr, AV.ptr, m, M, L, y.ptr, yp.ptr, active.ptr);
+      CU_LAUNCH_CHECK();
+      m = 2;
+    }
+    k32_save_yprev<<<B, 32, 0, st>>>(y.ptr, m, M, restart ? 1 : 0, active.ptr, yp.ptr);
+    CU_LAUNCH_CHECK();
+    // after a restart V changed: the first pass's dots are taken again
+    extend(m, false, !restart);
+  };
+  auto head = [&](int m, int it, int m_start, int rel, bool exact0) {
+    sigma_tc(ctx, bp, sw, V.ptr + (int64_t)(m - 1) * L, (int64_t)M * L,
+             AV.ptr + (int64_t)(m - 1) * L, (int64_t)M * L, active.ptr, shift);
+    dots(V.ptr, (int64_t)M * L, L, AV.ptr + (int64_t)(m - 1) * L, (int64_t)M * L, m, coef.ptr,
+         M, 1, active.ptr);
+    if (exact0) {
+      dot_comp(V.ptr, (int64_t)M * L, V.ptr + (int64_t)(m - 1) * L, (int64_t)M * L, cdot.ptr,
+               active.ptr);
+      dots(RX.ptr, L, 0, V.ptr + (int64_t)(m - 1) * L, (int64_t)M * L, 1, rdot.ptr, 1, 1,
+           active.ptr);
+    }
+    k32_store_row<<<B, 32, 0, st>>>(coef.ptr, cdot.ptr, rdot.ptr, thx.ptr, m, M, exact0 ? 1 : 0,
+                                    active.ptr, G.ptr);
+    CU_LAUNCH_CHECK();
+    k32_jacobi<<<B, 32, 0, st>>>(G.ptr, m, M, active.ptr, theta.ptr, y.ptr);
+    CU_LAUNCH_CHECK();
+    k32_residual_pre<<<gc, RT, (olsen ? 2 : 1) * m * RT * sizeof(float), st>>>(
+        V.ptr, AV.ptr, RX.ptr, exact0 ? 1 : 0, m, M, L, y.ptr, theta.ptr, thx.ptr, hd.ptr,
+        active.ptr, X.ptr, T.ptr, ch, nchunks, rpart.ptr, partial.ptr, olsen ? 1 : 0, U32.ptr,
+        upart.ptr, xpart.ptr);
+    CU_LAUNCH_CHECK();
+    k32_converge<<<1, 256, 0, st>>>(rpart.ptr, nchunks, B, m_start > 1 ? it + 1 : it, tolr.ptr,
+                                    rel, theta.ptr, rnorm.ptr, active.ptr, iters.ptr, nact.ptr);
+    CU_LAUNCH_CHECK();
+  };
+  // round_start: a refinement round's first correction (the preconditioned
+  // exact residual, appended as V_1) goes with the round's first head
+  auto round_start = [&] {
+    k32_copy_i<<<1, 256, 0, st>>>(active.ptr, mask.ptr, B);
+    CU_LAUNCH_CHECK();
+    CU_CHECK(cudaMemcpyAsync(T.ptr, RX.ptr, sizeof(float) * B * L, cudaMemcpyDeviceToDevice, st));
+    k32_save_yprev<<<B, 32, 0, st>>>(y.ptr, 1, M, 1, active.ptr, yp.ptr);
+    CU_LAUNCH_CHECK();
+    extend(1, true, false);
+  };
   auto stage = [&](int m_start, int cap, int rel, bool exact0, int nact0, int mcap) -> bool {
     int m = m_start, nact_h = nact0;
+    bool pending = false, restart = false;   // the tail still to issue
+    int m_tail = 0;
+    if (exact0 && (cap <= 0 || total_it >= max_iter)) round_start();
     for (int it = 0; it < cap && total_it < max_iter; it++, total_it++) {
-      sigma_tc(ctx, bp, sw, V.ptr + (int64_t)(m - 1) * L, (int64_t)M * L,
-               AV.ptr + (int64_t)(m - 1) * L, (int64_t)M * L, active.ptr, shift);
+      const bool pend = pending, rs = restart, pro = exact0 && it == 0;
+      const int mt = m_tail;
+      auto body = [&] {
+        if (pro) round_start();
+        if (pend) tail(mt, rs);
+        head(m, it, m_start, rel, exact0);
+      };
+      // the first iteration of a batch runs as plain launches: it makes the
+      // one-time set-up of the sigma path (tables, operand plans, the
+      // autotuner's timed launches), which synchronises
+      if (use_graphs && total_it >= 1)
+        gr.run((exact0 ? 1 : 0) | (pend ? 2 : 0) | (pend && rs ? 4 : 0) | (pro ? 8 : 0), body);
+      else
+        body();
+      pending = false;
       vecs_tc += nact_h;
-      dots(V.ptr, (int64_t)M * L, L, AV.ptr + (int64_t)(m - 1) * L, (int64_t)M * L, m, coef.ptr,
-           M, 1, active.ptr);
-      if (exact0) {
-        dot_comp(V.ptr, (int64_t)M * L, V.ptr + (int64_t)(m - 1) * L, (int64_t)M * L, cdot.ptr,
-                 active.ptr);
-        dots(RX.ptr, L, 0, V.ptr + (int64_t)(m - 1) * L, (int64_t)M * L, 1, rdot.ptr, 1, 1,
-             active.ptr);
-      }
-      k32_store_row<<<B, 32, 0, st>>>(coef.ptr, cdot.ptr, rdot.ptr, thx.ptr, m, M, exact0 ? 1 : 0,
-                                      active.ptr, G.ptr);
-      CU_LAUNCH_CHECK();
-      k32_jacobi<<<B, 32, 0, st>>>(G.ptr, m, M, active.ptr, theta.ptr, y.ptr);
-      CU_LAUNCH_CHECK();
-      k32_residual_pre<<<gc, RT, (olsen ? 2 : 1) * m * RT * sizeof(float), st>>>(
-          V.ptr, AV.ptr, RX.ptr, exact0 ? 1 : 0, m, M, L, y.ptr, theta.ptr, thx.ptr, hd.ptr,
-          active.ptr, X.ptr, T.ptr, ch, nchunks, rpart.ptr, partial.ptr, olsen ? 1 : 0, U32.ptr,
-          upart.ptr, xpart.ptr);
-      CU_LAUNCH_CHECK();
-      k32_converge<<<1, 256, 0, st>>>(rpart.ptr, nchunks, B, m_start > 1 ? it + 1 : it, tolr.ptr,
-                                      rel, theta.ptr, rnorm.ptr, active.ptr, iters.ptr, nact.ptr);
-      CU_LAUNCH_CHECK();
       nact_h = count_active();
       if (nact_h == 0) return false;
       if (exact0 && m == mcap) return true;
-      int restarted = 0;
-      if (m == mcap) {
-        k32_restart_coef<<<B, 32, 0, st>>>(y.ptr, yp.ptr, m, M, active.ptr, G.ptr);
-        CU_LAUNCH_CHECK();
-        k32_restart_vec<<<ge, 256, 0, st>>>(V.ptr, AV.ptr, m, M, L, y.ptr, yp.ptr, active.ptr);
-        CU_LAUNCH_CHECK();
-        m = 2;
-        restarted = 1;
-      }
-      k32_save_yprev<<<B, 32, 0, st>>>(y.ptr, m, M, restarted, active.ptr, yp.ptr);
-      CU_LAUNCH_CHECK();
-      // after a restart V changed: the first pass's dots are taken again
-      extend(m, false, !restarted);
-      m++;
+      restart = m == mcap;
+      m_tail = m;
+      pending = true;
+      m = (restart ? 2 : m) + 1;
     }
+    if (pending) tail(m_tail, restart);
     return false;
   };
   // the exact-point sigma: fused on the tensor cores where it fits (kpad <= 80)
@@ -1072,42 +1126,39 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
     CU_LAUNCH_CHECK();
   };
 
+  // the exact path's set-up before any of its calls is captured
+  if (exact_fused) sigma_exact_prepare(ctx, bp, sw);
   // stage A
   stage(1, 150, 1, false, B, Ms);
   // refinement rounds
   const double abs_target = ctx->opt.conv_tol_r, rel_target = ctx->opt.mixed_rel_tol;
   k32_fill_i<<<1, 256, 0, st>>>(mask.ptr, B, 1);
   CU_LAUNCH_CHECK();
-  std::vector<double> rn2(B);
   int round_cap = Ms;
   for (int round = 0; round < 12; round++) {
-    exact_point();
-    // rnorm holds |r_x|^2 sums: take the square root on the host side copy
-    CU_CHECK(cudaMemcpyAsync(rn2.data(), rnorm.ptr, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
-    CU_CHECK(cudaStreamSynchronize(st));
-    std::vector<int32_t> mk(B);
-    CU_CHECK(cudaMemcpy(mk.data(), mask.ptr, sizeof(int32_t) * B, cudaMemcpyDeviceToHost));
-    for (int b = 0; b < B; b++)
-      if (mk[b]) rn2[b] = std::sqrt(std::max(0.0, rn2[b]));
-    CU_CHECK(cudaMemcpyAsync(rnorm.ptr, rn2.data(), sizeof(double) * B, cudaMemcpyHostToDevice, st));
-    k32_select<<<1, 256, 0, st>>>(rnorm.ptr, mask.ptr, thx.ptr, B, abs_target, rel_target,
-                                  ctx->opt.mixed_round_drop, active.ptr, tolr.ptr, nact.ptr);
-    CU_LAUNCH_CHECK();
+    // the exact point and the selection of the tuples above their targets
+    // (one graph; the unfused FP64 path stages host data and runs plain)
+    auto point = [&] {
+      exact_point();
+      k32_select<<<1, 256, 0, st>>>(rnorm.ptr, mask.ptr, thx.ptr, B, abs_target, rel_target,
+                                    ctx->opt.mixed_round_drop, active.ptr, tolr.ptr, nact.ptr);
+      CU_LAUNCH_CHECK();
+    };
+    if (use_graphs && exact_fused)
+      gr.run(16, point);
+    else
+      point();
     const int na = count_active();
     if (ctx->opt.verbose) {
-      double t0 = 0.0;
+      double t0 = 0.0, r0 = 0.0;
       CU_CHECK(cudaMemcpy(&t0, thx.ptr, sizeof(double), cudaMemcpyDeviceToHost));
+      CU_CHECK(cudaMemcpy(&r0, rnorm.ptr, sizeof(double), cudaMemcpyDeviceToHost));
       fprintf(stderr, "[mbe mixed] exact point %d: %d above target; theta_x0=%.15f |r_x0|=%.3e\n",
-              round, na, t0, rn2[0]);
+              round, na, t0, r0);
     }
     if (na == 0 || total_it >= max_iter) break;
-    k32_copy_i<<<1, 256, 0, st>>>(active.ptr, mask.ptr, B);
-    CU_LAUNCH_CHECK();
-    // the exact residual, preconditioned, is the first correction
-    CU_CHECK(cudaMemcpyAsync(T.ptr, RX.ptr, sizeof(float) * B * L, cudaMemcpyDeviceToDevice, st));
-    k32_save_yprev<<<B, 32, 0, st>>>(y.ptr, 1, M, 1, active.ptr, yp.ptr);
-    CU_LAUNCH_CHECK();
-    extend(1, true, false);
+    // the exact residual, preconditioned, is the first correction: issued
+    // with the round's first iteration (round_start)
     // a round that filled its subspace before its tuples reached the target
     // (near-degenerate spaces) makes the later rounds use all M vectors
     if (stage(2, 40, 0, true, na, round_cap)) round_cap = M;
@@ -1156,6 +1207,8 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
     ctx->stats.noconv += ok ? 0 : 1;
   }
   const double per = 2.0 * (double)N * bp.npair * bp.npair;
+  ctx->stats.graph_launches += gr.launched;
+  ctx->stats.graph_builds += gr.instantiated;
   ctx->stats.casci += B;
   ctx->stats.sigma_vectors += vecs_tc + vecs_ex;
   ctx->stats.sigma_flops += (double)(vecs_tc + vecs_ex) * per;

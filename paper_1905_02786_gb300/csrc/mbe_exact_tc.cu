@@ -402,8 +402,7 @@ bool sigma_exact_supported(int npair, int nstr) {
   return ex_layout(kpad, R, nstr).total + 2048 <= 227 * 1024;
 }
 
-void sigma_exact(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const float* c, int64_t c_stride,
-                 double* X, int64_t x_stride, const int32_t* active) {
+void sigma_exact_prepare(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w) {
   const int npair = bp.npair, nstr = bp.nstr;
   const int kpad = ((npair + 15) / 16) * 16;
   const int R = nstr <= 2048 ? 2 : 1;
@@ -430,6 +429,16 @@ void sigma_exact(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const float* c, int
     CU_CHECK(cudaFuncSetAttribute(k_sigma_exact<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   227 * 1024 - 1024));
   });
+}
+
+void sigma_exact(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const float* c, int64_t c_stride,
+                 double* X, int64_t x_stride, const int32_t* active) {
+  const int npair = bp.npair, nstr = bp.nstr;
+  const int kpad = ((npair + 15) / 16) * 16;
+  const int R = nstr <= 2048 ? 2 : 1;
+  const ExShared L = ex_layout(kpad, R, nstr);
+  // one-time set-up of the batch (allocations, g' digit planes)
+  sigma_exact_prepare(ctx, bp, w);
   const dim3 grid((unsigned)((nstr + R - 1) / R), bp.B);
   cudaEvent_t ev;
   ctx->fp64_timer.begin(ctx->stream, ctx->opt.timing != 0, &ev);

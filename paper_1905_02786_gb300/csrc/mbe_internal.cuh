@@ -44,13 +44,36 @@ void once_per_device(bool (&done)[MBE_MAX_DEVICES], int device, F f) {
   done[device] = true;
 }
 
-// every launch site checks the launch and counts it
+// every launch site checks the launch and counts it: g_mbe_launches counts
+// kernels run on the device, g_mbe_host_launches the launch calls the host
+// makes (a replayed CUDA graph is one).  While this thread captures a graph
+// (GraphRunner) the launches are counted into t_capture_kernels instead and
+// added to g_mbe_launches each time the graph is launched.
 extern int64_t g_mbe_launches;
-#define CU_LAUNCH_CHECK()          \
-  do {                             \
-    __atomic_add_fetch(&g_mbe_launches, 1, __ATOMIC_RELAXED); \
-    CU_CHECK(cudaGetLastError());  \
+extern int64_t g_mbe_host_launches;
+extern thread_local bool t_capturing;
+extern thread_local int64_t t_capture_kernels;
+#define CU_LAUNCH_CHECK()                                          \
+  do {                                                             \
+    if (t_capturing) {                                             \
+      t_capture_kernels++;                                         \
+    } else {                                                       \
+      __atomic_add_fetch(&g_mbe_launches, 1, __ATOMIC_RELAXED);      \
+      __atomic_add_fetch(&g_mbe_host_launches, 1, __ATOMIC_RELAXED); \
+    }                                                              \
+    CU_CHECK(cudaGetLastError());                                  \
   } while (0)
+
+// a CUDA event recorded on s; inside a stream capture it becomes an event
+// record node of the graph (recorded each time the graph runs)
+inline void record_event(cudaEvent_t e, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cs);
+  if (cs == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+  else
+    cudaEventRecord(e, s);
+}
 
 // CUDA-event timing of the dominant (sigma contraction) kernel
 struct KernelTimer {
@@ -60,13 +83,13 @@ struct KernelTimer {
     *a = nullptr;
     if (!on) return;
     cudaEventCreate(a);
-    cudaEventRecord(*a, s);
+    record_event(*a, s);
   }
   void end(cudaStream_t s, cudaEvent_t a) {
     if (!a) return;
     cudaEvent_t b;
     cudaEventCreate(&b);
-    cudaEventRecord(b, s);
+    record_event(b, s);
     pending.emplace_back(a, b);
   }
   void resolve() {
@@ -79,6 +102,73 @@ struct KernelTimer {
       cudaEventDestroy(p.second);
     }
     pending.clear();
+  }
+};
+
+// ------------------------------------------------------------ CUDA graphs
+// Replays a launch sequence as one CUDA graph.  run(key, issue) records the
+// launches issue() makes on the stream (stream capture), brings the
+// executable graph kept for `key` up to date with them (cudaGraphExecUpdate
+// sets kernel arguments, grid shapes and events in place; a sequence of
+// another shape is instantiated anew) and launches it: one host launch for
+// the sequence, its kernels back to back on the device.  issue() must not
+// synchronise with the host (the capture fails with an error if it does).
+struct GraphRunner {
+  cudaStream_t st = nullptr;
+  std::map<int, cudaGraphExec_t> exec;
+  int64_t instantiated = 0, updated = 0, launched = 0;
+  explicit GraphRunner(cudaStream_t s) : st(s) {}
+  GraphRunner(const GraphRunner&) = delete;
+  GraphRunner& operator=(const GraphRunner&) = delete;
+  ~GraphRunner() {
+    for (auto& e : exec) cudaGraphExecDestroy(e.second);
+  }
+  template <class F>
+  void run(int key, F issue) {
+    CU_CHECK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    t_capturing = true;
+    t_capture_kernels = 0;
+    cudaGraph_t g = nullptr;
+    try {
+      issue();
+    } catch (...) {
+      t_capturing = false;
+      cudaStreamEndCapture(st, &g);
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      throw;
+    }
+    t_capturing = false;
+    const int64_t nk = t_capture_kernels;
+    CU_CHECK(cudaStreamEndCapture(st, &g));
+    auto it = exec.find(key);
+    bool ok = false;
+    if (it != exec.end()) {
+      cudaGraphExecUpdateResultInfo info;
+      if (cudaGraphExecUpdate(it->second, g, &info) == cudaSuccess) {
+        ok = true;
+        updated++;
+      } else {
+        cudaGetLastError();       // the update's error is not sticky
+        cudaGraphExecDestroy(it->second);
+        exec.erase(it);
+      }
+    }
+    if (!ok) {
+      cudaGraphExec_t e = nullptr;
+      const cudaError_t r = cudaGraphInstantiate(&e, g, 0);
+      if (r != cudaSuccess) {
+        cudaGraphDestroy(g);
+        throw MbeError{MBE_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(r)};
+      }
+      exec[key] = e;
+      instantiated++;
+    }
+    cudaGraphDestroy(g);
+    CU_CHECK(cudaGraphLaunch(exec[key], st));
+    launched++;
+    __atomic_add_fetch(&g_mbe_launches, nk, __ATOMIC_RELAXED);
+    __atomic_add_fetch(&g_mbe_host_launches, 1, __ATOMIC_RELAXED);
   }
 };
 
@@ -213,7 +303,7 @@ struct OrderRec {
 struct mbe_ctx {
   int device = 0;
   mbe_stats stats = {};
-  int64_t launch_base = 0;
+  int64_t launch_base = 0, host_launch_base = 0;
   KernelTimer dom_timer;     // tensor-core sigma launches
   KernelTimer fp64_timer;    // FP64 contraction launches
   mbe_options opt;
@@ -391,6 +481,9 @@ bool ozaki_supported(int npair);
 // tensor cores: writes the rows X (sigma = X + X^T + shift S^2 c follows in
 // launch_finish_sym_fp64)
 bool sigma_exact_supported(int npair, int nstr);
+// the fused exact sigma's one-time set-up of a batch (buffers, g' digit
+// planes; sigma_exact makes it on its first call when this was not called)
+void sigma_exact_prepare(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w);
 void sigma_exact(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const float* c, int64_t c_stride,
                  double* X, int64_t x_stride, const int32_t* active);
 // out = X + X^T + shift S^2 c in place for every tuple of the batch (c = c^T)

@@ -1015,7 +1015,12 @@ void sigma_tc(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const float* c, int64_
     }
   }
   if (w.Xf.n < (size_t)B * N) w.Xf.reset(&ctx->pool, (size_t)B * N);
-  if (!w.err.ptr) w.err.reset(&ctx->pool, 1);
+  // the timeout word is cleared once, when it is allocated: a timeout of
+  // any call of the batch stays visible to sigma_tc_error
+  if (!w.err.ptr) {
+    w.err.reset(&ctx->pool, 1);
+    CU_CHECK(cudaMemsetAsync(w.err.ptr, 0, sizeof(int32_t), st));
+  }
   if (w.csplit.n < (size_t)B * hs * 2) w.csplit.reset(&ctx->pool, (size_t)B * hs * 2);
   // per batch (constant over the Davidson iteration): g'/2 split and H^a
   const size_t gbytes = (size_t)B * 2 * p.kp * p.kp * 2;
@@ -1037,7 +1042,6 @@ void sigma_tc(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const float* c, int64_
                                                           bp.gp.ptr, p.ldc, (bf16*)bp.haa.ptr, hs);
     CU_LAUNCH_CHECK();
   }
-  CU_CHECK(cudaMemsetAsync(w.err.ptr, 0, sizeof(int32_t), st));
   bf16* cs = (bf16*)w.csplit.ptr;
   {
     const int64_t work = (int64_t)nstr * (p.ldc / 8);

@@ -42,12 +42,14 @@ def test_options_struct_matches_header_defaults():
     assert o.max_subspace == 20 and o.spin_shift == 0.5 and o.deterministic == 1
     assert (o.mixed_stage_tol, o.mixed_round_drop, o.mixed_rel_tol) == (1e-5, 1e-2, 2e-7)
     assert o.pspace == 128
+    assert o.autotune == 0 and o.graphs == 1 and o.wait_limit == 1 << 24
 
 
 @pytest.mark.parametrize("field,value", [("mixed_stage_tol", 0.0), ("mixed_round_drop", 1.0),
                                          ("mixed_round_drop", 0.0), ("mixed_rel_tol", -1.0),
                                          ("max_subspace", 33), ("pspace", 129),
-                                         ("pspace", -1)])
+                                         ("pspace", -1), ("graphs", 2), ("graphs", -1),
+                                         ("autotune", 3)])
 def test_create_rejects_bad_options(field, value):
     """Options are checked before any device call, so this runs without a GPU."""
     from paper_1905_02786_gb300 import _binding
