@@ -42,10 +42,13 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;
 }
 
-// Every vector of the mixed Davidson iteration has L elements (N_det rounded
-// up to a multiple of 4, the padding kept at zero) and starts on a 16-byte
-// boundary, so the streaming kernels below move float4s.  A reduction chunk
-// is `ch` elements (a multiple of 1024, chosen per batch).
+// Every FP32 vector of the mixed Davidson iteration is alpha-beta symmetric
+// and kept packed (sym_index): L = sym_len(nstr) elements, about half of
+// N_det, the padding kept at zero, each vector on a 16-byte boundary, so the
+// streaming kernels below move float4s.  Their dot products weigh the
+// float4s from nd4 = sym_nd / 4 on (the upper triangle) by 2, which gives
+// the dot products of the full vectors.  A reduction chunk is `ch` elements
+// (a multiple of 1024, chosen per batch).
 
 __device__ __forceinline__ float dot4(const float4 a, const float4 b, float acc) {
   acc = fmaf(a.x, b.x, acc);
@@ -54,10 +57,10 @@ __device__ __forceinline__ float dot4(const float4 a, const float4 b, float acc)
   return fmaf(a.w, b.w, acc);
 }
 
-// partial[b][i][chunk] = sum over the chunk of X[b][i][k] Y[b][k], i < m
+// partial[b][i][chunk] = sum over the chunk of w_k X[b][i][k] Y[b][k], i < m
 __global__ void __launch_bounds__(RT) k32_multidot(const float* __restrict__ X, int64_t xb,
                                                   int64_t xv, const float* __restrict__ Y,
-                                                  int64_t yb, int m, int64_t L, int ch,
+                                                  int64_t yb, int m, int64_t L, int64_t nd4, int ch,
                                                   int nchunks, const int32_t* __restrict__ active,
                                                   double* __restrict__ partial) {
   const int b = blockIdx.y;
@@ -73,7 +76,9 @@ __global__ void __launch_bounds__(RT) k32_multidot(const float* __restrict__ X, 
 #pragma unroll
     for (int i = 0; i < 16; i++) acc[i] = 0.f;
     for (int64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
-      const float4 yv = y[q];
+      const float4 y0 = y[q];
+      const float w = q < nd4 ? 1.f : 2.f;        // exact scaling
+      const float4 yv = make_float4(w * y0.x, w * y0.y, w * y0.z, w * y0.w);
 #pragma unroll
       for (int i = 0; i < 16; i++)
         if (i < ni)
@@ -99,7 +104,7 @@ __global__ void __launch_bounds__(RT) k32_multidot(const float* __restrict__ X, 
 // error-free dot of two FP32 vectors: products split exactly (p + e = x y),
 // the p terms summed with compensation, all per-thread sums combined in FP64
 __global__ void k32_dot_comp(const float* __restrict__ X, int64_t xb, const float* __restrict__ Y,
-                             int64_t yb, int64_t N, int ch, int nchunks,
+                             int64_t yb, int64_t N, int64_t nd, int ch, int nchunks,
                              const int32_t* __restrict__ active, double* __restrict__ partial) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
@@ -112,7 +117,7 @@ __global__ void k32_dot_comp(const float* __restrict__ X, int64_t xb, const floa
   // exactly (TwoSum: s + p = t + err)
   float s = 0.f, lo = 0.f;
   for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
-    const float a = x[k], bb = y[k];
+    const float a = x[k] * (k < nd ? 1.f : 2.f), bb = y[k];   // weight: exact
     const float p = a * bb;
     const float e = fmaf(a, bb, -p);
     const float t = s + p;
@@ -188,49 +193,21 @@ __global__ void k32_converge(const double* __restrict__ partial, int nchunks, in
   if (threadIdx.x == 0) *nactive = cnt;
 }
 
-// t = r / (theta - H_II), symmetrised over (Ia, Ib) <-> (Ib, Ia)
-// 32 x 32 tiles (I, J) and (J, I), I <= J, staged in shared memory so that
-// both the element and its transpose are read and written coalesced
-__global__ void k32_precondition(float* __restrict__ T, const float* __restrict__ hd, int nstr,
-                                 int64_t ld, const double* __restrict__ theta,
+// t = r / (theta - H_II) on the packed vector (the full vector's
+// symmetrised correction: r and H_II are symmetric)
+__global__ void k32_precondition(float* __restrict__ T, const float* __restrict__ hd, int64_t L,
+                                 const double* __restrict__ theta,
                                  const int32_t* __restrict__ active) {
   const int b = blockIdx.y;
   if (!active[b]) return;
-  // tile pair index -> (I, J), I <= J, row-major over the upper triangle
-  const int nt = (nstr + 31) / 32;
-  int t = blockIdx.x, I = 0;
-  while (t >= nt - I) {
-    t -= nt - I;
-    I++;
-  }
-  const int J = I + t;
-  __shared__ float sT[2][32][33], sH[2][32][33];
   const float th = (float)theta[b];
-  float* Tb = T + (int64_t)b * ld;
-  const float* hb = hd + (int64_t)b * ld;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
-  for (int h = 0; h < 2; h++) {
-    const int r0 = (h ? J : I) * 32, c0 = (h ? I : J) * 32;
-    for (int i = ty; i < 32; i += 8) {
-      const int row = r0 + i, col = c0 + tx;
-      const bool in = row < nstr && col < nstr;
-      sT[h][i][tx] = in ? Tb[(int64_t)row * nstr + col] : 0.f;
-      sH[h][i][tx] = in ? hb[(int64_t)row * nstr + col] : 0.f;
-    }
-  }
-  __syncthreads();
-  // element (I*32 + i, J*32 + j) pairs with (J*32 + j, I*32 + i) = sT[1][j][i]
-  for (int h = 0; h < 2; h++) {
-    const int r0 = (h ? J : I) * 32, c0 = (h ? I : J) * 32;
-    for (int i = ty; i < 32; i += 8) {
-      const int row = r0 + i, col = c0 + tx;
-      if (row >= nstr || col >= nstr) continue;
-      float d1 = th - sH[h][i][tx], d2 = th - sH[1 - h][tx][i];
-      if (fabsf(d1) < 1e-4f) d1 = d1 < 0.f ? -1e-4f : 1e-4f;
-      if (fabsf(d2) < 1e-4f) d2 = d2 < 0.f ? -1e-4f : 1e-4f;
-      Tb[(int64_t)row * nstr + col] = 0.5f * (sT[h][i][tx] / d1 + sT[1 - h][tx][i] / d2);
-    }
-    if (I == J) break;   // a diagonal tile is its own transpose
+  float* Tb = T + (int64_t)b * L;
+  const float* hb = hd + (int64_t)b * L;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < L;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    float d = th - hb[k];
+    if (fabsf(d) < 1e-4f) d = d < 0.f ? -1e-4f : 1e-4f;
+    Tb[k] = Tb[k] / d;
   }
 }
 
@@ -307,14 +284,13 @@ __device__ __forceinline__ void sde_sums_to_partial(const float2 (*sDE)[RT], int
 //   x = V y,  r = AV y - theta x (stage A), or with exact0
 //   r = y_0 (r_x + (theta_x - theta) V_0) + sum_{i>=1} y_i (AV_i - theta V_i),
 //   |r|^2 partials,
-//   t = r / (theta - H_II)  (every vector is alpha-beta symmetric bitwise, so
-//       this equals the symmetrised form of k32_precondition),
+//   t = r / (theta - H_II)  (as k32_precondition),
 //   partials of V_i . t, i < m.
 // The second read of V_i[k] follows the first within the same thread and is
 // served by the caches, so V streams from HBM once instead of twice.
 __global__ void __launch_bounds__(RT) k32_residual_pre(
     const float* __restrict__ V, const float* __restrict__ AV, const float* __restrict__ RX,
-    int exact0, int m, int M, int64_t L, const double* __restrict__ y,
+    int exact0, int m, int M, int64_t L, int64_t nd4, const double* __restrict__ y,
     const double* __restrict__ theta, const double* __restrict__ thx,
     const float* __restrict__ hd, const int32_t* __restrict__ active, float* __restrict__ X,
     float* __restrict__ T, int ch, int nchunks, double* __restrict__ rpart,
@@ -372,37 +348,40 @@ __global__ void __launch_bounds__(RT) k32_residual_pre(
     Xb[q] = make_float4(xs[0], xs[1], xs[2], xs[3]);
     const float4 h4 = hb[q];
     const float hv[4] = {h4.x, h4.y, h4.z, h4.w};
+    const float w = q < nd4 ? 1.f : 2.f;          // weight of the packed elements
     float ts[4], us[4];
 #pragma unroll
     for (int e = 0; e < 4; e++) {
-      acc = fmaf(rs[e], rs[e], acc);
+      acc = fmaf(w * rs[e], rs[e], acc);
       float d = th - hv[e];
       if (fabsf(d) < 1e-4f) d = d < 0.f ? -1e-4f : 1e-4f;
       ts[e] = rs[e] / d;
       us[e] = xs[e] / d;
     }
     const float4 t = make_float4(ts[0], ts[1], ts[2], ts[3]);
+    const float4 tw = make_float4(w * ts[0], w * ts[1], w * ts[2], w * ts[3]);
     Tb[q] = t;
     if (olsen) {
       const float4 u = make_float4(us[0], us[1], us[2], us[3]);
+      const float4 uw = make_float4(w * us[0], w * us[1], w * us[2], w * us[3]);
       Ub[q] = u;
 #pragma unroll
       for (int e = 0; e < 4; e++) {
-        xt = fmaf(xs[e], ts[e], xt);
-        xu = fmaf(xs[e], us[e], xu);
+        xt = fmaf(w * xs[e], ts[e], xt);
+        xu = fmaf(w * xs[e], us[e], xu);
       }
 #pragma unroll 4
       for (int i = 0; i < m; i++) {
         const float4 v = Vb[(int64_t)i * Lq + q];
         float2 a = sDE[i][threadIdx.x];
-        a.x = dot4(v, t, a.x);
-        a.y = dot4(v, u, a.y);
+        a.x = dot4(v, tw, a.x);
+        a.y = dot4(v, uw, a.y);
         sDE[i][threadIdx.x] = a;
       }
     } else {
 #pragma unroll 4
       for (int i = 0; i < m; i++)
-        sD[i][threadIdx.x] = dot4(Vb[(int64_t)i * Lq + q], t, sD[i][threadIdx.x]);
+        sD[i][threadIdx.x] = dot4(Vb[(int64_t)i * Lq + q], tw, sD[i][threadIdx.x]);
     }
   }
   const double tot = block_sum((double)acc, red);
@@ -458,7 +437,8 @@ __global__ void k32_sub_eps(float* __restrict__ T, const float* __restrict__ U,
 //   norm == 1: partials of T . T (the normalisation).
 __global__ void __launch_bounds__(RT) k32_orth_pass(float* __restrict__ T,
                                                    const float* __restrict__ V, int m, int M,
-                                                   int64_t L, const double* __restrict__ coef,
+                                                   int64_t L, int64_t nd4,
+                                                   const double* __restrict__ coef,
                                                    const int32_t* __restrict__ active, int norm,
                                                    int ch, int nchunks, double* __restrict__ partial,
                                                    const float* __restrict__ Uo,
@@ -496,12 +476,14 @@ __global__ void __launch_bounds__(RT) k32_orth_pass(float* __restrict__ T,
                       fmaf(-c, v.w, t.w));
     }
     Tb[q] = t;
+    const float w = q < nd4 ? 1.f : 2.f;          // weight of the packed elements
+    const float4 tw = make_float4(w * t.x, w * t.y, w * t.z, w * t.w);
     if (norm) {
-      nacc = dot4(t, t, nacc);
+      nacc = dot4(t, tw, nacc);
     } else {
 #pragma unroll 4
       for (int i = 0; i < m; i++)
-        sD[i][threadIdx.x] = dot4(Vb[(int64_t)i * Lq + q], t, sD[i][threadIdx.x]);
+        sD[i][threadIdx.x] = dot4(Vb[(int64_t)i * Lq + q], tw, sD[i][threadIdx.x]);
     }
   }
   if (norm) {
@@ -654,6 +636,7 @@ __global__ void k32_hdiag(const uint32_t* __restrict__ masks, int nstr, int64_t 
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int ia = (int)(i / nstr), ib = (int)(i - (int64_t)ia * nstr);
+    if (ia > ib) continue;                      // packed: the upper triangle
     const uint32_t ma = masks[ia], mb = masks[ib], mu = ma | mb;
     float cross = 0.f;
     for (uint32_t mp = mu; mp; mp &= mp - 1) {
@@ -665,7 +648,7 @@ __global__ void k32_hdiag(const uint32_t* __restrict__ masks, int nstr, int64_t 
         if (w) cross = fmaf((float)w, sJ[p * n + q], cross);
       }
     }
-    hd_all[(int64_t)b * ld + i] =
+    hd_all[(int64_t)b * ld + sym_index(ia, ib, nstr)] =
         (eb[ia] + eb[ib]) + cross + shift * (float)(nsig - __popc(ma & mb));
   }
 }
@@ -679,7 +662,9 @@ __global__ void k32_guess(const float* __restrict__ hd, int nstr, int64_t ld, in
   float best = 3.4e38f;
   int64_t bi = 0;
   for (int64_t k = threadIdx.x; k < N; k += blockDim.x) {
-    const float v = hd[(int64_t)b * ld + k];
+    const int ia = (int)(k / nstr), ib = (int)(k - (int64_t)ia * nstr);
+    if (ia > ib) continue;   // the mirror element has the same value, a larger k
+    const float v = hd[(int64_t)b * ld + sym_index(ia, ib, nstr)];
     if (v < best) { best = v; bi = k; }
   }
   sv[threadIdx.x] = best;
@@ -702,17 +687,16 @@ __global__ void k32_guess(const float* __restrict__ hd, int nstr, int64_t ld, in
   if (threadIdx.x == 0) {
     const int64_t i0 = si[0];
     const int ia = (int)(i0 / nstr), ib = (int)(i0 % nstr);
-    if (ia == ib) Vb[i0] = 1.f;
-    else {
-      Vb[(int64_t)ia * nstr + ib] = 0.70710678f;
-      Vb[(int64_t)ib * nstr + ia] = 0.70710678f;
-    }
+    // (|a b> + |b a>) / sqrt(2): its packed element carries both halves
+    Vb[sym_index(ia, ib, nstr)] = ia == ib ? 1.f : 0.70710678f;
   }
 }
 
-// V0 = X / |X| (FP32) and its FP64 copy C64 (input of the exact sigma)
+// V0 = X / |X|: packed into V (slot 0), full into F (FP32, input of the
+// exact sigma) and C64 (its FP64 copy); Lf is the stride of the full vectors
 __global__ void k32_exact_prep(const float* __restrict__ X, const double* __restrict__ xx,
-                               float* __restrict__ V, int M, double* __restrict__ C64, int64_t N,
+                               float* __restrict__ V, int M, int64_t L, float* __restrict__ F,
+                               double* __restrict__ C64, int64_t Lf, int nstr,
                                const int32_t* __restrict__ active) {
   const int b = blockIdx.y;
   if (!active[b]) return;
@@ -720,11 +704,30 @@ __global__ void k32_exact_prep(const float* __restrict__ X, const double* __rest
   if (threadIdx.x == 0) s_inv = (float)(1.0 / sqrt(xx[b]));   // one FP64 root per block
   __syncthreads();
   const float inv = s_inv;
+  const int64_t N = (int64_t)nstr * nstr;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N;
        k += (int64_t)gridDim.x * blockDim.x) {
-    const float v = X[(int64_t)b * N + k] * inv;
-    V[(int64_t)b * M * N + k] = v;
-    C64[(int64_t)b * N + k] = (double)v;
+    const int ia = (int)(k / nstr), ib = (int)(k - (int64_t)ia * nstr);
+    const int64_t p = sym_index(ia, ib, nstr);
+    const float v = X[(int64_t)b * L + p] * inv;
+    F[(int64_t)b * Lf + k] = v;
+    C64[(int64_t)b * Lf + k] = (double)v;
+    if (ia <= ib) V[(int64_t)b * M * L + p] = v;
+  }
+}
+
+// start vectors of the tuples in plan_mask: the full FP32 vectors F (stride
+// Lf) written by the parent guess, packed into V (slot 0)
+__global__ void k32_pack_start(const float* __restrict__ F, int64_t Lf,
+                               const int32_t* __restrict__ plan_mask, int nstr, int M, int64_t L,
+                               float* __restrict__ V) {
+  const int b = blockIdx.y;
+  if (!plan_mask[b]) return;
+  const int64_t N = (int64_t)nstr * nstr;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int ia = (int)(k / nstr), ib = (int)(k - (int64_t)ia * nstr);
+    if (ia <= ib) V[(int64_t)b * M * L + sym_index(ia, ib, nstr)] = F[(int64_t)b * Lf + k];
   }
 }
 
@@ -744,10 +747,11 @@ __global__ void k32_exact_xax(const double* __restrict__ C64, const double* __re
 }
 
 // r_x = A V0 - theta_x V0 (stored FP32) and partial sums of |r_x|^2
+// (C64, S64 full, stride N; RX packed, stride L)
 __global__ void k32_exact_rx(const double* __restrict__ C64, const double* __restrict__ S64,
                              const double* __restrict__ thx, int64_t N, int ch, int nchunks,
                              const int32_t* __restrict__ active, float* __restrict__ RX,
-                             double* __restrict__ partial) {
+                             int64_t L, int nstr, double* __restrict__ partial) {
   const int b = blockIdx.y;
   if (!active[b]) return;
   __shared__ double red[32];
@@ -756,7 +760,8 @@ __global__ void k32_exact_rx(const double* __restrict__ C64, const double* __res
   double acc = 0.0;
   for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
     const double r = fma(-th, C64[(int64_t)b * N + k], S64[(int64_t)b * N + k]);
-    RX[(int64_t)b * N + k] = (float)r;
+    const int ia = (int)(k / nstr), ib = (int)(k - (int64_t)ia * nstr);
+    if (ia <= ib && ia < nstr) RX[(int64_t)b * L + sym_index(ia, ib, nstr)] = (float)r;
     acc = fma(r, r, acc);
   }
   const double tot = block_sum(acc, red);
@@ -828,10 +833,13 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
   // its subspace full and tuples still above their targets
   const int Ms = std::max(4, std::min(32, ctx->opt.max_subspace));
   const int M = mixed_subspace_alloc(ctx->opt.max_subspace);
-  // N determinants per tuple; every vector takes L = N rounded up to a
-  // multiple of 4 elements (the padding stays zero: the sigma and diagonal
-  // kernels never write it, and every combination of zero elements is zero)
-  const int64_t N = bp.ndet, L = (N + 3) / 4 * 4;
+  // N determinants per tuple; every FP32 Davidson vector is packed (L =
+  // sym_len elements), the FP64 exact-point vectors and the FP32 input of the
+  // exact sigma are full (Lf = N rounded up to a multiple of 4).  Padding
+  // stays zero: no kernel writes it, and every combination of zero elements
+  // is zero.
+  const int64_t N = bp.ndet, L = sym_len(bp.nstr), Lf = (N + 3) / 4 * 4;
+  const int64_t nd4 = sym_nd(bp.nstr) / 4;
   const double shift = ctx->opt.spin_shift;
   DevPool* P = &ctx->pool;
   const int nsm = [&] {
@@ -844,28 +852,30 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
   int ch = 16384;
   while (ch > 1024 && (int64_t)B * ((L + ch - 1) / ch) < 4 * (int64_t)nsm) ch >>= 1;
   const int nchunks = (int)((L + ch - 1) / ch);
+  const int nchunks_f = (int)((Lf + ch - 1) / ch);   // chunks of the full FP64 vectors
   DevBuf<float> V(P, (size_t)B * M * L), AV(P, (size_t)B * M * L), hd(P, (size_t)B * L),
-      T(P, (size_t)B * L), X(P, (size_t)B * L), RX(P, (size_t)B * L);
-  DevBuf<double> C64(P, (size_t)B * L), S64(P, (size_t)B * L),
+      T(P, (size_t)B * L), X(P, (size_t)B * L), RX(P, (size_t)B * L), F(P, (size_t)B * Lf);
+  DevBuf<double> C64(P, (size_t)B * Lf), S64(P, (size_t)B * Lf),
       G(P, (size_t)B * M * M), y(P, (size_t)B * M), yp(P, (size_t)B * M), theta(P, B),
       thx(P, B), rnorm(P, B), tolr(P, B), coef(P, (size_t)B * M), cdot(P, B), rdot(P, B),
-      xx(P, B), xax(P, B), partial(P, (size_t)B * M * nchunks), rpart(P, (size_t)B * nchunks);
+      xx(P, B), xax(P, B), partial(P, (size_t)B * M * nchunks),
+      rpart(P, (size_t)B * std::max(nchunks, nchunks_f));
   DevBuf<int32_t> active(P, B), iters(P, B), nact(P, 1), mask(P, B);
   SigmaWork sw;
   cudaStream_t st = ctx->stream;
-  if (L != N) {
-    // zero padding (the vectors' tails are read by the streaming kernels)
-    CU_CHECK(cudaMemsetAsync(V.ptr, 0, sizeof(float) * B * M * L, st));
-    CU_CHECK(cudaMemsetAsync(AV.ptr, 0, sizeof(float) * B * M * L, st));
-    CU_CHECK(cudaMemsetAsync(hd.ptr, 0, sizeof(float) * B * L, st));
-    CU_CHECK(cudaMemsetAsync(RX.ptr, 0, sizeof(float) * B * L, st));
-    CU_CHECK(cudaMemsetAsync(C64.ptr, 0, sizeof(double) * B * L, st));
-    CU_CHECK(cudaMemsetAsync(S64.ptr, 0, sizeof(double) * B * L, st));
+  // zero padding (the vectors' tails are read by the streaming kernels)
+  CU_CHECK(cudaMemsetAsync(V.ptr, 0, sizeof(float) * B * M * L, st));
+  CU_CHECK(cudaMemsetAsync(AV.ptr, 0, sizeof(float) * B * M * L, st));
+  CU_CHECK(cudaMemsetAsync(hd.ptr, 0, sizeof(float) * B * L, st));
+  CU_CHECK(cudaMemsetAsync(RX.ptr, 0, sizeof(float) * B * L, st));
+  if (Lf != N) {
+    CU_CHECK(cudaMemsetAsync(F.ptr, 0, sizeof(float) * B * Lf, st));
+    CU_CHECK(cudaMemsetAsync(C64.ptr, 0, sizeof(double) * B * Lf, st));
+    CU_CHECK(cudaMemsetAsync(S64.ptr, 0, sizeof(double) * B * Lf, st));
   }
   const int64_t eb = std::min<int64_t>((L + 255) / 256, 1024);
-  const dim3 ge((unsigned)eb, B), gc(nchunks, B);
-  const int ntl = (bp.nstr + 31) / 32;
-  const dim3 gpre((unsigned)(ntl * (ntl + 1) / 2), B);
+  const int64_t ebf = std::min<int64_t>((Lf + 255) / 256, 1024);
+  const dim3 ge((unsigned)eb, B), gef((unsigned)ebf, B), gc(nchunks, B), gcf(nchunks_f, B);
   const int max_iter = std::max(1, ctx->opt.max_iter);
   int total_it = 0;
   int64_t vecs_tc = 0, vecs_ex = 0;
@@ -876,7 +886,7 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
     k32_string_energy<<<dim3((unsigned)((bp.nstr + 255) / 256), B), 256, 0, st>>>(
         bp.tab->masks.ptr, bp.nstr, bp.n, bp.heff.ptr, bp.jk.ptr, estr.ptr);
     CU_LAUNCH_CHECK();
-    k32_hdiag<<<ge, 256, 0, st>>>(bp.tab->masks.ptr, bp.nstr, L, bp.n, bp.nsig, bp.jk.ptr,
+    k32_hdiag<<<gef, 256, 0, st>>>(bp.tab->masks.ptr, bp.nstr, L, bp.n, bp.nsig, bp.jk.ptr,
                                   estr.ptr, (float)shift, hd.ptr);
     CU_LAUNCH_CHECK();
   }
@@ -900,7 +910,17 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
   }
   k32_guess<<<B, 256, 0, st>>>(hd.ptr, bp.nstr, L, M, V.ptr);
   CU_LAUNCH_CHECK();
-  if (plan) launch_parent_guess(ctx, *plan, bp.n, bp.nsig, bp.nstr, V.ptr, nullptr, (int64_t)M * L);
+  if (plan) {
+    // the parent guess writes full vectors (into F), packed into V_0 here
+    launch_parent_guess(ctx, *plan, bp.n, bp.nsig, bp.nstr, F.ptr, nullptr, Lf);
+    std::vector<int32_t> pm(B, 0);
+    for (int b : plan->b) pm[b] = 1;
+    DevBuf<int32_t> pmask(P, B);
+    CU_CHECK(cudaMemcpyAsync(pmask.ptr, pm.data(), sizeof(int32_t) * B, cudaMemcpyHostToDevice, st));
+    k32_pack_start<<<gef, 256, 0, st>>>(F.ptr, Lf, pmask.ptr, bp.nstr, M, L, V.ptr);
+    CU_LAUNCH_CHECK();
+    CU_CHECK(cudaStreamSynchronize(st));   // pm is read by the copy above
+  }
   k32_fill_i<<<1, 256, 0, st>>>(active.ptr, B, 1);
   CU_LAUNCH_CHECK();
   CU_CHECK(cudaMemsetAsync(iters.ptr, 0, sizeof(int32_t) * B, st));
@@ -910,15 +930,15 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
 
   auto dots = [&](const float* Xv, int64_t xb, int64_t xv, const float* Yv, int64_t yb, int m,
                   double* out, int64_t ob, int64_t oi, const int32_t* act) {
-    k32_multidot<<<dim3(nchunks, B), RT, 0, st>>>(Xv, xb, xv, Yv, yb, m, L, ch, nchunks, act,
-                                                   partial.ptr);
+    k32_multidot<<<dim3(nchunks, B), RT, 0, st>>>(Xv, xb, xv, Yv, yb, m, L, nd4, ch, nchunks,
+                                                   act, partial.ptr);
     CU_LAUNCH_CHECK();
     k32_final<<<B, 32, 0, st>>>(partial.ptr, m, nchunks, act, out, ob, oi);
     CU_LAUNCH_CHECK();
   };
   auto dot_comp = [&](const float* Xv, int64_t xb, const float* Yv, int64_t yb, double* out,
                       const int32_t* act) {
-    k32_dot_comp<<<dim3(nchunks, B), RT, 0, st>>>(Xv, xb, Yv, yb, L, ch, nchunks, act,
+    k32_dot_comp<<<dim3(nchunks, B), RT, 0, st>>>(Xv, xb, Yv, yb, L, 4 * nd4, ch, nchunks, act,
                                                    partial.ptr);
     CU_LAUNCH_CHECK();
     k32_final<<<B, 32, 0, st>>>(partial.ptr, 1, nchunks, act, out, 1, 1);
@@ -946,7 +966,7 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
   // replaced first (the dot partials corrected with it).
   auto extend = [&](int m, bool raw, bool dots_ready) {
     if (raw) {
-      k32_precondition<<<gpre, 256, 0, st>>>(T.ptr, hd.ptr, bp.nstr, L, theta.ptr, active.ptr);
+      k32_precondition<<<ge, 256, 0, st>>>(T.ptr, hd.ptr, L, theta.ptr, active.ptr);
       CU_LAUNCH_CHECK();
     }
     // Olsen's combination goes with the P-space block (its exact block would
@@ -979,7 +999,7 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
     }
     for (int pass = 0; pass < 2; pass++) {
       const bool fold = ols && dots_ready && pass == 0;   // t = t1 - eps u inside the pass
-      k32_orth_pass<<<gc, RT, 0, st>>>(T.ptr, V.ptr, m, M, L, coef.ptr, active.ptr, pass, ch,
+      k32_orth_pass<<<gc, RT, 0, st>>>(T.ptr, V.ptr, m, M, L, nd4, coef.ptr, active.ptr, pass, ch,
                                       nchunks, partial.ptr, fold ? U32.ptr : nullptr,
                                       epsb.ptr);
       CU_LAUNCH_CHECK();
@@ -1026,7 +1046,7 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
   };
   auto head = [&](int m, int it, int m_start, int rel, bool exact0) {
     sigma_tc(ctx, bp, sw, V.ptr + (int64_t)(m - 1) * L, (int64_t)M * L,
-             AV.ptr + (int64_t)(m - 1) * L, (int64_t)M * L, active.ptr, shift);
+             AV.ptr + (int64_t)(m - 1) * L, (int64_t)M * L, active.ptr, shift, true);
     dots(V.ptr, (int64_t)M * L, L, AV.ptr + (int64_t)(m - 1) * L, (int64_t)M * L, m, coef.ptr,
          M, 1, active.ptr);
     if (exact0) {
@@ -1041,7 +1061,7 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
     k32_jacobi<<<B, 32, 0, st>>>(G.ptr, m, M, active.ptr, theta.ptr, y.ptr);
     CU_LAUNCH_CHECK();
     k32_residual_pre<<<gc, RT, (olsen ? 2 : 1) * m * RT * sizeof(float), st>>>(
-        V.ptr, AV.ptr, RX.ptr, exact0 ? 1 : 0, m, M, L, y.ptr, theta.ptr, thx.ptr, hd.ptr,
+        V.ptr, AV.ptr, RX.ptr, exact0 ? 1 : 0, m, M, L, nd4, y.ptr, theta.ptr, thx.ptr, hd.ptr,
         active.ptr, X.ptr, T.ptr, ch, nchunks, rpart.ptr, partial.ptr, olsen ? 1 : 0, U32.ptr,
         upart.ptr, xpart.ptr);
     CU_LAUNCH_CHECK();
@@ -1100,29 +1120,31 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
     k32_copy_i<<<1, 256, 0, st>>>(mask.ptr, active.ptr, B);
     CU_LAUNCH_CHECK();
     dot_comp(X.ptr, L, X.ptr, L, xx.ptr, active.ptr);
-    k32_exact_prep<<<ge, 256, 0, st>>>(X.ptr, xx.ptr, V.ptr, M, C64.ptr, L, active.ptr);
+    k32_exact_prep<<<gef, 256, 0, st>>>(X.ptr, xx.ptr, V.ptr, M, L, F.ptr, C64.ptr, Lf, bp.nstr,
+                                        active.ptr);
     CU_LAUNCH_CHECK();
     dot_comp(V.ptr, (int64_t)M * L, V.ptr, (int64_t)M * L, xx.ptr, active.ptr);
     if (exact_fused) {
-      sigma_exact(ctx, bp, sw, V.ptr, (int64_t)M * L, S64.ptr, L, active.ptr);
-      launch_finish_sym_fp64(ctx, bp, S64.ptr, L, C64.ptr, L, shift, active.ptr);
+      sigma_exact(ctx, bp, sw, F.ptr, Lf, S64.ptr, Lf, active.ptr);
+      launch_finish_sym_fp64(ctx, bp, S64.ptr, Lf, C64.ptr, Lf, shift, active.ptr);
     } else {
-      sigma_fp64(ctx, bp, sw, C64.ptr, L, S64.ptr, L, active.ptr, shift, true, true);
+      sigma_fp64(ctx, bp, sw, C64.ptr, Lf, S64.ptr, Lf, active.ptr, shift, true, true);
     }
     vecs_ex += B;
-    k32_exact_xax<<<gc, RT, 0, st>>>(C64.ptr, S64.ptr, L, ch, nchunks, active.ptr, rpart.ptr);
+    k32_exact_xax<<<gcf, RT, 0, st>>>(C64.ptr, S64.ptr, Lf, ch, nchunks_f, active.ptr,
+                                      rpart.ptr);
     CU_LAUNCH_CHECK();
-    k32_final<<<B, 32, 0, st>>>(rpart.ptr, 1, nchunks, active.ptr, xax.ptr, 1, 1);
+    k32_final<<<B, 32, 0, st>>>(rpart.ptr, 1, nchunks_f, active.ptr, xax.ptr, 1, 1);
     CU_LAUNCH_CHECK();
     // theta_x first (the residual needs it), then r_x and its norm
     k32_exact_fin<<<(B + 127) / 128, 128, 0, st>>>(xax.ptr, xx.ptr, rpart.ptr, 0, M, B,
                                                    active.ptr, thx.ptr, theta.ptr, G.ptr,
                                                    rnorm.ptr, iters.ptr);
     CU_LAUNCH_CHECK();
-    k32_exact_rx<<<gc, RT, 0, st>>>(C64.ptr, S64.ptr, thx.ptr, L, ch, nchunks, active.ptr, RX.ptr,
-                                    rpart.ptr);
+    k32_exact_rx<<<gcf, RT, 0, st>>>(C64.ptr, S64.ptr, thx.ptr, Lf, ch, nchunks_f, active.ptr,
+                                     RX.ptr, L, bp.nstr, rpart.ptr);
     CU_LAUNCH_CHECK();
-    k32_final<<<B, 32, 0, st>>>(rpart.ptr, 1, nchunks, active.ptr, rnorm.ptr, 1, 1);
+    k32_final<<<B, 32, 0, st>>>(rpart.ptr, 1, nchunks_f, active.ptr, rnorm.ptr, 1, 1);
     CU_LAUNCH_CHECK();
   };
 
@@ -1166,7 +1188,7 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
   if (sigma_tc_error(ctx, sw)) throw MbeError{MBE_ETIMEOUT, "tensor-core sigma wait timed out"};
 
   // energies: E = E_core + theta_x - shift <S^2> (S^2 of the exact-point vector, FP64)
-  s2_apply(ctx, bp, C64.ptr, L, S64.ptr, L, nullptr);
+  s2_apply(ctx, bp, C64.ptr, Lf, S64.ptr, Lf, nullptr);
   std::vector<double> th(B), ec(B), rn(B), s2(B), nx(B);
   std::vector<int32_t> it_h(B);
   {
@@ -1174,13 +1196,13 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
     DevBuf<int32_t> all(P, B);
     k32_fill_i<<<1, 256, 0, st>>>(all.ptr, B, 1);
     CU_LAUNCH_CHECK();
-    k32_exact_xax<<<gc, RT, 0, st>>>(C64.ptr, S64.ptr, L, ch, nchunks, all.ptr, rpart.ptr);
+    k32_exact_xax<<<gcf, RT, 0, st>>>(C64.ptr, S64.ptr, Lf, ch, nchunks_f, all.ptr, rpart.ptr);
     CU_LAUNCH_CHECK();
-    k32_final<<<B, 32, 0, st>>>(rpart.ptr, 1, nchunks, all.ptr, coef.ptr, 1, 1);
+    k32_final<<<B, 32, 0, st>>>(rpart.ptr, 1, nchunks_f, all.ptr, coef.ptr, 1, 1);
     CU_LAUNCH_CHECK();
-    k32_exact_xax<<<gc, RT, 0, st>>>(C64.ptr, C64.ptr, L, ch, nchunks, all.ptr, rpart.ptr);
+    k32_exact_xax<<<gcf, RT, 0, st>>>(C64.ptr, C64.ptr, Lf, ch, nchunks_f, all.ptr, rpart.ptr);
     CU_LAUNCH_CHECK();
-    k32_final<<<B, 32, 0, st>>>(rpart.ptr, 1, nchunks, all.ptr, xax.ptr, 1, 1);
+    k32_final<<<B, 32, 0, st>>>(rpart.ptr, 1, nchunks_f, all.ptr, xax.ptr, 1, 1);
     CU_LAUNCH_CHECK();
   }
   CU_CHECK(cudaMemcpyAsync(th.data(), thx.ptr, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
@@ -1190,7 +1212,7 @@ void davidson_batch_mixed(mbe_ctx* ctx, BinProblem& bp, double* e_out_host, int3
   CU_CHECK(cudaMemcpyAsync(nx.data(), xax.ptr, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
   CU_CHECK(cudaMemcpyAsync(it_h.data(), iters.ptr, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, st));
   if (x_out_dev)
-    CU_CHECK(cudaMemcpy2DAsync(x_out_dev, sizeof(double) * N, C64.ptr, sizeof(double) * L,
+    CU_CHECK(cudaMemcpy2DAsync(x_out_dev, sizeof(double) * N, C64.ptr, sizeof(double) * Lf,
                                sizeof(double) * N, B, cudaMemcpyDeviceToDevice, st));
   CU_CHECK(cudaStreamSynchronize(st));
 

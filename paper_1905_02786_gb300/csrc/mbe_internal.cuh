@@ -105,6 +105,28 @@ struct KernelTimer {
   }
 };
 
+// ------------------------------------------------- packed symmetric vectors
+// The mixed Davidson keeps its FP32 vectors of a closed-shell M_s = 0 space
+// (c(a, b) = c(b, a)) packed: the nstr diagonal elements first, padded to
+// sym_nd = nstr rounded up to 4, then the strictly upper triangle row by row;
+// sym_len elements in all (a multiple of 4, the padding zero).  A dot
+// product of two such vectors weighs the upper elements by 2, so it equals
+// the dot product of the full vectors.
+__host__ __device__ inline int sym_nd(int nstr) { return (nstr + 3) & ~3; }
+__host__ __device__ inline int64_t sym_len(int nstr) {
+  return ((int64_t)sym_nd(nstr) + (int64_t)nstr * (nstr - 1) / 2 + 3) & ~(int64_t)3;
+}
+// packed position of element (a, b) or (b, a)
+__host__ __device__ inline int64_t sym_index(int a, int b, int nstr) {
+  if (a > b) {
+    const int t = a;
+    a = b;
+    b = t;
+  }
+  return a == b ? (int64_t)a
+                : (int64_t)sym_nd(nstr) + (int64_t)a * (2 * nstr - a - 1) / 2 + (b - a - 1);
+}
+
 // ------------------------------------------------------------ CUDA graphs
 // Replays a launch sequence as one CUDA graph.  run(key, issue) records the
 // launches issue() makes on the stream (stream capture), brings the
@@ -451,8 +473,10 @@ struct SigmaWork {
 };
 bool sigma_tc_supported(int n, int nstr);
 // FP32 vectors in and out (c = c^T assumed: sigma = X + X^T)
+// packed: c and the result in the packed symmetric layout (sym_index)
 void sigma_tc(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const float* c, int64_t c_stride,
-              float* out, int64_t out_stride, const int32_t* active, double spin_shift);
+              float* out, int64_t out_stride, const int32_t* active, double spin_shift,
+              bool packed = false);
 int32_t sigma_tc_error(mbe_ctx* ctx, SigmaWork& w);
 // subspace vectors allocated per tuple by the mixed Davidson: max_subspace
 // (clamped to 4..32) for its first stage and its refinement rounds, up to 12

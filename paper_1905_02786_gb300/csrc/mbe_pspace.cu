@@ -20,7 +20,7 @@
 // per iteration:
 //   k_psp_apply   t_P = U (theta - Lambda)^{-1} U^T r_P (r_P recovered from
 //                 the diagonal correction as t_I (theta - A_II)), written
-//                 back bitwise symmetric, and the first Gram-Schmidt pass's
+//                 back into the packed vector, and the first Gram-Schmidt pass's
 //                 dot products corrected for the changed elements; the same
 //                 for M^-1 x, x the Ritz vector.
 // With an exact block M^-1 r = -x on P whenever x lies in P and does not
@@ -68,7 +68,9 @@ __device__ __forceinline__ int block_flag_scan(bool f, int* s_warp, int* total) 
 }
 
 // psel[b][0..npp) = linear indices a nstr + c (a <= c) of the npp canonical
-// pairs of lowest diagonal, in increasing index order
+// pairs of lowest diagonal, in increasing index order (the diagonal and all
+// vectors are in the packed symmetric layout, element (a, c) at
+// sym_index(a, c))
 __global__ void __launch_bounds__(SEL_THREADS)
     k_psp_select(const float* __restrict__ hd_all, int nstr, int64_t ld, int npp,
                  int32_t* __restrict__ psel) {
@@ -87,7 +89,7 @@ __global__ void __launch_bounds__(SEL_THREADS)
     for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
       const int a = (int)(i / nstr), c = (int)(i - (int64_t)a * nstr);
       if (a > c) continue;
-      const uint32_t key = order_key(hd[i]);
+      const uint32_t key = order_key(hd[sym_index(a, c, nstr)]);
       if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
     }
     __syncthreads();
@@ -117,7 +119,7 @@ __global__ void __launch_bounds__(SEL_THREADS)
     if (i < N) {
       const int a = (int)(i / nstr), c = (int)(i - (int64_t)a * nstr);
       if (a <= c) {
-        const uint32_t key = order_key(hd[i]);
+        const uint32_t key = order_key(hd[sym_index(a, c, nstr)]);
         lt = key < thr;
         eq = key == thr;
       }
@@ -258,7 +260,7 @@ __global__ void __launch_bounds__(EIG_THREADS)
     s_ma[u] = masks[a];
     s_mb[u] = masks[c];
     s_diag[u] = a == c;
-    s_hd[u] = hd_all[(int64_t)b * ld + i];
+    s_hd[u] = hd_all[(int64_t)b * ld + sym_index(a, c, nstr)];
   }
   // an odd npp gets one decoupled pad index (zero row and column)
   const int m = (npp + 1) & ~1;
@@ -415,8 +417,9 @@ __global__ void __launch_bounds__(APPLY_THREADS)
   }
   const float sq2 = 1.41421356237309505f, r2 = 0.70710678118654752f;
   for (int u = tid; u < npp; u += blockDim.x) {
-    const int i = psel[(int64_t)b * PSP_MAX + u];
-    const int a = i / nstr, c = i - a * nstr;
+    const int i0 = psel[(int64_t)b * PSP_MAX + u];
+    const int a = i0 / nstr, c = i0 - a * nstr;
+    const int i = (int)sym_index(a, c, nstr);          // packed position
     // the diagonal correction's denominator, exactly as the residual kernel
     float d = th - hb[i];
     if (fabsf(d) < 1e-4f) d = d < 0.f ? -1e-4f : 1e-4f;
@@ -451,18 +454,15 @@ __global__ void __launch_bounds__(APPLY_THREADS)
       if (olsen) yx = fmaf(uk, s_wx[k], yx);
     }
     const int i = s_i[u];
-    const int a = i / nstr, c = i - a * nstr;
-    const int64_t i2 = (int64_t)c * nstr + a;
-    const float f = a == c ? 1.f : 2.f;   // both elements of a pair change alike
-    const float tn = a == c ? y : y * r2;
+    const bool diag = i < sym_nd(nstr);
+    const float f = diag ? 1.f : 2.f;   // both elements of a pair change alike
+    const float tn = diag ? y : y * r2;
     s_del[u] = (tn - Tb[i]) * f;
     Tb[i] = tn;
-    Tb[i2] = tn;   // the same value: t stays bitwise symmetric
     if (olsen) {
-      const float un = a == c ? yx : yx * r2;
+      const float un = diag ? yx : yx * r2;
       s_delu[u] = (un - Ob[i]) * f;
       Ob[i] = un;
-      Ob[i2] = un;
     }
   }
   __syncthreads();

@@ -103,6 +103,55 @@ __global__ void k_split_c(const float* __restrict__ c, int64_t c_stride, int nst
   }
 }
 
+// the same from a packed symmetric vector (sym_index layout): one CTA per
+// 32 x 32 tile pair (I, J), I <= J, reads tile (I, J) from the packed rows
+// (coalesced) and writes the rows of both tiles, the transposed one through
+// shared memory; the values are those k_split_c gives for the full vector
+__global__ void k_split_c_sym(const float* __restrict__ c, int64_t c_stride, int nstr, int ldc,
+                              const int32_t* __restrict__ active, bf16* __restrict__ cs,
+                              int64_t cs_stride) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const int nt = (nstr + 31) / 32;
+  int t = blockIdx.x, I = 0;
+  while (t >= nt - I) {
+    t -= nt - I;
+    I++;
+  }
+  const int J = I + t;
+  __shared__ float sC[32][33];
+  const float* cb = c + (int64_t)b * c_stride;
+  bf16* hi = cs + (int64_t)b * cs_stride;
+  bf16* lo = hi + (int64_t)nstr * ldc;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5, ny = blockDim.x >> 5;
+  for (int i = ty; i < 32; i += ny) {
+    const int r = I * 32 + i, k = J * 32 + tx;
+    sC[i][tx] = (r < nstr && k < nstr) ? cb[sym_index(r, k, nstr)] : 0.f;
+  }
+  __syncthreads();
+  // rows of tile I, columns of tile J (zeros from nstr up to ldc)
+  for (int i = ty; i < 32; i += ny) {
+    const int r = I * 32 + i, k = J * 32 + tx;
+    if (r < nstr && k < ldc) {
+      const float x = sC[i][tx];
+      const bf16 h = __float2bfloat16_rn(x);
+      hi[(int64_t)r * ldc + k] = h;
+      lo[(int64_t)r * ldc + k] = __float2bfloat16_rn(x - __bfloat162float(h));
+    }
+  }
+  if (I == J) return;
+  // rows of tile J, columns of tile I (all below nstr)
+  for (int i = ty; i < 32; i += ny) {
+    const int r = J * 32 + i, k = I * 32 + tx;
+    if (r < nstr) {
+      const float x = sC[tx][i];
+      const bf16 h = __float2bfloat16_rn(x);
+      hi[(int64_t)r * ldc + k] = h;
+      lo[(int64_t)r * ldc + k] = __float2bfloat16_rn(x - __bfloat162float(h));
+    }
+  }
+}
+
 // ------------------------------------------------------------ g'/2 split
 // gh[b] = {hi[kp][kp], lo[kp][kp]}: bf16 split of g'/2 (zero beyond npair);
 // the factor 1/2 of W = H^a c + Z/2 (exact: a power of two)
@@ -781,12 +830,13 @@ k_sigma_ab(const int32_t* __restrict__ lnk, const int16_t* __restrict__ plist,
 // sigma is symmetric: one CTA per 32 x 32 tile pair (I, J), I <= J, forms
 // the values of tile (I, J) once (the spin term's gathers of c are the cost
 // of this kernel) and writes them to both tiles, the transpose through
-// shared memory so that every store is coalesced.
+// shared memory so that every store is coalesced.  packed: c and sigma in
+// the packed symmetric layout (sym_index), only tile (I, J) is written.
 __global__ void k_sigma_tc_finish(const float* __restrict__ X, int64_t x_stride,
                                   const int32_t* __restrict__ link, const uint32_t* __restrict__ masks,
                                   int nstr, int n, int nsig, const float* __restrict__ c,
                                   int64_t c_stride, float shift, const int32_t* __restrict__ active,
-                                  float* __restrict__ out, int64_t out_stride) {
+                                  float* __restrict__ out, int64_t out_stride, int packed) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
   const int nt = (nstr + 31) / 32;
@@ -822,7 +872,8 @@ __global__ void k_sigma_tc_finish(const float* __restrict__ X, int64_t x_stride,
       const int32_t* la = link + (int64_t)lo * npair;
       const int32_t* lb = link + (int64_t)hi * npair;
       const uint32_t ma = masks[lo], mb = masks[hi];
-      float s2 = (float)(nsig - __popc(ma & mb)) * cb[(int64_t)lo * nstr + hi];
+      float s2 = (float)(nsig - __popc(ma & mb)) *
+                 cb[packed ? sym_index(lo, hi, nstr) : (int64_t)lo * nstr + hi];
       // pairs {p, q}: q open in the alpha string, p open in the beta string
       uint32_t oa = ma & ~mb;
       const uint32_t obm = mb & ~ma;
@@ -835,16 +886,22 @@ __global__ void k_sigma_tc_finish(const float* __restrict__ X, int64_t x_stride,
           ob2 &= ob2 - 1;
           const int P = p > q ? p * (p + 1) / 2 + q : q * (q + 1) / 2 + p;
           const int32_t ta = la[P], tb = lb[P];
-          const float x = cb[(int64_t)(ta >> 1) * nstr + (tb >> 1)];
+          const float x = cb[packed ? sym_index(ta >> 1, tb >> 1, nstr)
+                                    : (int64_t)(ta >> 1) * nstr + (tb >> 1)];
           s2 -= ((ta ^ tb) & 1) ? -x : x;
         }
       }
       s += shift * s2;
     }
     v[k] = s;
-    if (ia < nstr && ib < nstr) ob[(int64_t)ia * nstr + ib] = s;
+    if (ia < nstr && ib < nstr) {
+      if (!packed)
+        ob[(int64_t)ia * nstr + ib] = s;
+      else if (ia <= ib)
+        ob[sym_index(ia, ib, nstr)] = s;
+    }
   }
-  if (I == J) return;                                // the tile was its own transpose
+  if (I == J || packed) return;                      // the tile was its own transpose
   __syncthreads();
   for (int k = 0, i = ty; i < 32; i += ny, k++) sX[0][i][tx] = v[k];
   __syncthreads();
@@ -978,7 +1035,8 @@ bool sigma_tc_supported(int n, int nstr) {
 }
 
 void sigma_tc(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const float* c, int64_t c_stride,
-              float* out, int64_t out_stride, const int32_t* active, double spin_shift) {
+              float* out, int64_t out_stride, const int32_t* active, double spin_shift,
+              bool packed) {
   const int npair = bp.npair, nstr = bp.nstr, B = bp.B;
   const int nsm = sm_count(ctx->device);
   AbPlan p;
@@ -1043,7 +1101,12 @@ void sigma_tc(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const float* c, int64_
     CU_LAUNCH_CHECK();
   }
   bf16* cs = (bf16*)w.csplit.ptr;
-  {
+  if (packed) {
+    const int ntp = (nstr + 31) / 32;
+    k_split_c_sym<<<dim3((unsigned)(ntp * (ntp + 1) / 2), B), 256, 0, st>>>(c, c_stride, nstr,
+                                                                           p.ldc, active, cs, hs);
+    CU_LAUNCH_CHECK();
+  } else {
     const int64_t work = (int64_t)nstr * (p.ldc / 8);
     const unsigned gx = (unsigned)std::min<int64_t>((work + 255) / 256, 1024);
     k_split_c<<<dim3(gx, B), 256, 0, st>>>(c, c_stride, nstr, p.ldc, active, cs, hs);
@@ -1130,7 +1193,8 @@ void sigma_tc(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const float* c, int64_
   const int ntl = (nstr + 31) / 32;
   k_sigma_tc_finish<<<dim3((unsigned)(ntl * (ntl + 1) / 2), B), 256, 0, st>>>(w.Xf.ptr, N, bp.tab->link.ptr, bp.tab->masks.ptr,
                                                 nstr, bp.n, bp.nsig, c, c_stride,
-                                                (float)spin_shift, active, out, out_stride);
+                                                (float)spin_shift, active, out, out_stride,
+                                                packed ? 1 : 0);
   CU_LAUNCH_CHECK();
 }
 
