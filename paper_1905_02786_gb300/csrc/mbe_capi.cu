@@ -192,15 +192,17 @@ void solve_jobs(mbe_ctx* ctx, const std::vector<std::vector<int>>& acts, double*
     StringTables* tabb = nsigb == nsig ? tab : get_tables(ctx, n, nsigb);
     const bool closed = tabb == tab;
     const int64_t N = (int64_t)tab->nstr * tabb->nstr;
-    // device bytes per tuple: the mixed Davidson holds V and AV (M vectors
-    // each) and five work vectors in FP32 plus two FP64 exact-point vectors,
-    // the bf16 hi/lo copies of the sigma operand and of H^alpha and the
-    // P-space eigenvectors; the FP64 one 2M + 6 FP64 vectors
+    // device bytes per tuple: the mixed Davidson holds V and AV (M packed
+    // vectors each, N/2 FP32 elements) and five packed FP32 work vectors,
+    // the full FP32 exact-point operand, two full FP64 exact-point vectors,
+    // the FP32 W rows of the sigma, the bf16 hi/lo copies of the sigma
+    // operand and of H^alpha and the P-space eigenvectors; the FP64 one
+    // 2M + 6 FP64 vectors
     // the mixed path works on alpha<->beta symmetric vectors: closed shells
     const bool mixed_bin = ctx->opt.precision == MBE_MIXED_BF16X3 && N > 1 && closed &&
                            sigma_tc_supported(n, tab->nstr) && ozaki_supported(tab->npair);
     const int Mm = mixed_subspace_alloc(ctx->opt.max_subspace);
-    double per = (mixed_bin ? (double)(8 * Mm + 46) * N + 128.0 * 129.0 * 4.0
+    double per = (mixed_bin ? (double)(4 * Mm + 46) * N + 128.0 * 129.0 * 4.0
                             : (double)(2 * M + 6) * N * 8.0) +
                  (double)tab->npair * tab->npair * 8.0 * 2.0;
     int64_t bmem = std::max<int64_t>(1, (int64_t)(budget / per));
