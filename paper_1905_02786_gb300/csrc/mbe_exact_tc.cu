@@ -6,7 +6,9 @@
 // The exact point vector c is FP32 (its values are taken as exact), so
 //   D_P(a,k) = s_a c(J_a, k) + s_k c(a, J_k)
 // is the exact sum of two FP32 numbers.  Per determinant m = (a, k) of a
-// tile, e_m bounds |d_1| + |d_2| over all pairs P (|.| < 2^e_m) and
+// tile, e_m bounds |d_1| + |d_2| over all pairs P (|.| < 2^e_m): from the
+// largest |c| of row k and of row a (|d_1| <= max_j |c(j, k)|, |d_2| <=
+// max_j |c(a, j)|, c = c^T; k_rowmax), and
 //   F_P(m) = round(d_1 2^(39 - e_m)) + round(d_2 2^(39 - e_m))   (|F| <= 2^39)
 // is cut into five balanced 8-bit digits, exact in bf16; g' is cut the same
 // way per row with exponent e_P (once per batch, k_slice_gp_exact).  Every
@@ -21,7 +23,7 @@
 // (|c| <= 1 gives e_m <= 2, so |X| < 2^60 units and each contribution is I
 // shifted right by at least 7 bits, rounded).  The rows of X are written in
 // FP64; sigma = X + X^T + shift S^2 c follows in k_finish_sym_fp64.  Each
-// term carries an error of at most 2^-49 of the largest |g'|.
+// term carries an error of at most 2^-38 (2^(e_m - 40)) of the largest |g'|.
 //
 // Layout of a tile, as in the tensor-core sigma: M = 128 determinants
 // (R rows a of X per CTA, W = 128 / R column strings k), N = kpad pairs,
@@ -133,6 +135,20 @@ __global__ void k_slice_gp_exact(const double* __restrict__ gp_all, int npair, i
   }
 }
 
+// rmax[b][a] = max_k |c(a, k)| (one warp per row)
+__global__ void k_rowmax(const float* __restrict__ c, int64_t c_stride, int nstr,
+                         const int32_t* __restrict__ active, float* __restrict__ rmax) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const int a = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (a >= nstr) return;
+  const float* row = c + (int64_t)b * c_stride + (int64_t)a * nstr;
+  float m = 0.f;
+  for (int k = lane; k < nstr; k += 32) m = fmaxf(m, fabsf(row[k]));
+  for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) rmax[(int64_t)b * nstr + a] = m;
+}
+
 struct ExShared {
   uint32_t g, d, c_rows, x_rows, link_k, link_a, ep, em, total;
 };
@@ -162,9 +178,9 @@ template <int R>
 __global__ void __launch_bounds__(EX_THREADS, 1)
 k_sigma_exact(const int32_t* __restrict__ link, int nstr, int npair, int kpad,
               const uint8_t* __restrict__ gslices, const int32_t* __restrict__ ge,
-              const float* __restrict__ c, int64_t c_stride, const int32_t* __restrict__ active,
-              double* __restrict__ X, int64_t x_stride, long long wait_limit,
-              int32_t* __restrict__ err) {
+              const float* __restrict__ c, int64_t c_stride, const float* __restrict__ rmax,
+              const int32_t* __restrict__ active, double* __restrict__ X, int64_t x_stride,
+              long long wait_limit, int32_t* __restrict__ err) {
   constexpr int W = EX_M / R;
   const int LS = ex_link_stride(kpad);
   const int b = blockIdx.y;
@@ -272,26 +288,15 @@ k_sigma_exact(const int32_t* __restrict__ link, int nstr, int npair, int kpad,
         dst[P] = (uint16_t)(t < 0 ? nstr : ((t >> 1) | ((t & 1) << 15)));
       }
     }
-    if (tid < EX_M) sEm[tid] = -1000;
     __syncthreads();
     const int k = k0 + gj;
     const bool col_ok = ga < nstr && k < nstr;
     const uint16_t* lkg = sLk + gj * LS;
-    // ---- pass 1: e_m from max_P (|d_1| + |d_2|)
+    // ---- digit planes of D (A operand), e_m from the row maxima of c
     {
-      int e = -1000;
-      for (int kb = tid >> 7; kb < nkb; kb += EX_THREADS / EX_M) {
-        float d1[8], d2[8];
-        terms(k, col_ok, kb * 8, lkg, d1, d2);
-#pragma unroll
-        for (int q = 0; q < 8; q++) e = max(e, exp_f32(fabsf(d1[q]) + fabsf(d2[q])));
-      }
-      atomicMax(&sEm[gm], e);
-    }
-    __syncthreads();
-    // ---- pass 2: digit planes of D (A operand)
-    {
-      const int e = sEm[gm];
+      const int e = col_ok ? exp_f32(rmax[(int64_t)b * nstr + ga] + rmax[(int64_t)b * nstr + k])
+                           : -1000;
+      if (tid < EX_M) sEm[gm] = e;
       for (int kb = tid >> 7; kb < nkb; kb += EX_THREADS / EX_M) {
         float d1[8], d2[8];
         terms(k, col_ok, kb * 8, lkg, d1, d2);
@@ -422,6 +427,7 @@ void sigma_exact_prepare(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w) {
                                                              w.gexp.ptr);
     CU_LAUNCH_CHECK();
   }
+  if (w.rmax.n < (size_t)bp.B * nstr) w.rmax.reset(&ctx->pool, (size_t)bp.B * nstr);
   static bool attr_done[MBE_MAX_DEVICES] = {false};
   once_per_device(attr_done, ctx->device, [] {
     CU_CHECK(cudaFuncSetAttribute(k_sigma_exact<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -442,14 +448,17 @@ void sigma_exact(mbe_ctx* ctx, BinProblem& bp, SigmaWork& w, const float* c, int
   const dim3 grid((unsigned)((nstr + R - 1) / R), bp.B);
   cudaEvent_t ev;
   ctx->fp64_timer.begin(ctx->stream, ctx->opt.timing != 0, &ev);
+  k_rowmax<<<dim3((unsigned)((nstr + 7) / 8), bp.B), 256, 0, ctx->stream>>>(c, c_stride, nstr,
+                                                                          active, w.rmax.ptr);
+  CU_LAUNCH_CHECK();
   if (R == 2)
     k_sigma_exact<2><<<grid, EX_THREADS, L.total, ctx->stream>>>(
-        bp.tab->link.ptr, nstr, npair, kpad, w.gex.ptr, w.gexp.ptr, c, c_stride, active, X,
-        x_stride, ctx->opt.wait_limit, w.err.ptr);
+        bp.tab->link.ptr, nstr, npair, kpad, w.gex.ptr, w.gexp.ptr, c, c_stride, w.rmax.ptr,
+        active, X, x_stride, ctx->opt.wait_limit, w.err.ptr);
   else
     k_sigma_exact<1><<<grid, EX_THREADS, L.total, ctx->stream>>>(
-        bp.tab->link.ptr, nstr, npair, kpad, w.gex.ptr, w.gexp.ptr, c, c_stride, active, X,
-        x_stride, ctx->opt.wait_limit, w.err.ptr);
+        bp.tab->link.ptr, nstr, npair, kpad, w.gex.ptr, w.gexp.ptr, c, c_stride, w.rmax.ptr,
+        active, X, x_stride, ctx->opt.wait_limit, w.err.ptr);
   CU_LAUNCH_CHECK();
   ctx->fp64_timer.end(ctx->stream, ev);
   ctx->stats.fp64_launches += 1;

@@ -469,6 +469,7 @@ struct SigmaWork {
   DevBuf<int32_t> err;           // timeout flag of the tensor-core path
   DevBuf<uint8_t> gex;           // g' digit planes of the fused exact sigma
   DevBuf<int32_t> gexp;          // their row exponents
+  DevBuf<float> rmax;            // largest |c| per row (exact sigma's digit scales)
   int64_t sub_batch = 0;
 };
 bool sigma_tc_supported(int n, int nstr);
