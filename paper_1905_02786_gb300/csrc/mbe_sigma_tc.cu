@@ -225,12 +225,14 @@ k_build_haa(const int32_t* __restrict__ link, int nstr, int npair, const double*
 
 // ------------------------------------------------------------ W = H^a c
 // Tiles of 128 x 128 (rows a of H^a x rows b of c = columns b of c), K in
-// blocks of 32 through a 4-stage cp.async ring loaded two blocks ahead (a
-// stage is refilled once the MMAs of two blocks earlier have completed);
+// blocks of 32 through a 3-stage cp.async ring loaded two blocks ahead (a
+// stage is refilled once the MMAs of the block before have completed; 97 KB
+// of shared memory, so two CTAs share an SM: 4 stages, one CTA per SM, were
+// 0.7 % slower on the 64 x 8e/12o batch);
 // both operands K-major (8 rows x 16 bytes core matrices, LBO 128, SBO 512);
 // one elected thread issues the split-BF16x3 MMAs into a 128-column TMEM
 // accumulator.
-constexpr int GM_T = 128, GK_T = 32, G_STAGES = 4, G_AHEAD = 2, G_THREADS = 128;
+constexpr int GM_T = 128, GK_T = 32, G_STAGES = 3, G_AHEAD = 2, G_THREADS = 128;
 constexpr uint32_t G_OPB = GM_T * GK_T * 2;          // bytes of one operand half (8 KB)
 constexpr uint32_t G_STAGE = 4 * G_OPB;              // A hi, A lo, B hi, B lo
 constexpr uint32_t G_SMEM = G_STAGES * G_STAGE + 1024;
