@@ -43,10 +43,10 @@ DEFAULT_WORKLOAD = "h2o_dz_8e23o"
 # kernel definition is unchanged (sha256 prefix of its source text).  From
 # the captures of one launch over 64 active 8e/12o tuples (1.9081e+11 flop),
 # profiles/k_sigma_ab_8e12o_batch64.md.
-TRAFFIC = {"k_gemm_haa": {"bytes_per_flop": (125788672 + 37701376) / 1.9081e11,
-                          "sha": "fc8f06c321a2b658"},
-           "k_sigma_ab": {"bytes_per_flop": (99887872 + 9439744) / 1.9081e11,
-                          "sha": "a498f9b7eb8ce26f"}}
+TRAFFIC = {"k_gemm_haa": {"bytes_per_flop": (126411008 + 33256448) / 1.9081e11,
+                          "sha": "230b4e42ae85e619"},
+           "k_sigma_ab": {"bytes_per_flop": (100085760 + 9144576) / 1.9081e11,
+                          "sha": "b562c774055038dc"}}
 
 
 def peaks():
@@ -59,14 +59,16 @@ def peaks():
 
 def src_sha(path, kernel=None):
     """sha256 prefix of a source file, or of one kernel's definition in it
-    (from its signature line to the first line that is a lone closing brace)."""
+    (from its signature line to the first line that is a lone closing brace)
+    together with the file's constexpr lines (tile sizes, stages, threads)."""
     text = open(os.path.join(ROOT, path)).read()
     if kernel:
         lines = text.splitlines()
         start = next(i for i, l in enumerate(lines) if l.startswith(kernel + "(")
                      or (" " + kernel + "(") in l and "__global__" in l)
         end = next(i for i in range(start, len(lines)) if lines[i] == "}")
-        text = "\n".join(lines[start:end + 1])
+        consts = [l for l in lines if l.startswith("constexpr")]
+        text = "\n".join(lines[start:end + 1] + consts)
     return hashlib.sha256(text.encode()).hexdigest()[:16]
 
 
